@@ -1,0 +1,154 @@
+/*
+ * hk.h -- C ABI of libhk: the smallest eigenvalue of the Hankel moment matrix
+ * H_N = (mu_{i+j}), mu_j = Gamma((j+1)/beta)/beta, by extreme-precision LDL^T
+ * (arXiv 1810.01478, Secs. 2 and 4), on one GB300 GPU (sm_103a).
+ *
+ * Number format.  Every multiprecision value is a radix-2^32 float with n
+ * limbs (n = bits/32):  value = (-1)^sign * (sum_k limb[k] 2^(32k)) * 2^(32*exp),
+ * limbs little endian, the top limb (k = n-1) non-zero, or all limbs zero for
+ * the value 0 (then sign = exp = 0).  Every operation of the path forms its
+ * exact result and truncates the magnitude toward zero to n limbs (the
+ * "compute exactly, then truncate" rule of Sec. 4.1 applied to a floating
+ * format).  `bits` must be a multiple of 1024 with 32 <= n <= 1024 among the
+ * compiled widths (hk_supported_bits).
+ *
+ * Arrays of numbers cross the boundary as three parallel arrays
+ * (structure of arrays): int32 sign[count], int32 exp[count] and
+ * uint32 limbs[count * n] (number i occupies limbs[i*n .. i*n+n)).
+ *
+ * Ownership.  A context owns all device memory it allocates (cudaMalloc) and
+ * frees it in hk_destroy.  Host buffers are owned by the caller; the library
+ * reads or writes them only during the call.  Device buffers passed to the
+ * elementwise primitives are owned by the caller.
+ *
+ * Streams.  Every call is ordered on the cudaStream_t given to hk_create
+ * (borrowed, never destroyed).  hk_lambda1, hk_lambda1_grad and hk_export
+ * synchronise that stream; the other calls only enqueue work.
+ *
+ * Errors.  Calls return hk_status; nothing aborts, traps or throws.  The
+ * context keeps the first error (sticky) and hk_last_error describes it.
+ * Device-side failures (a non-positive pivot, an exhausted correction loop)
+ * are raised as flags in device memory and reported by the next
+ * synchronising call.
+ */
+#ifndef HK_H
+#define HK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define HK_API __attribute__((visibility("default")))
+#else
+#define HK_API
+#endif
+
+typedef struct hk_ctx hk_ctx;
+
+typedef enum hk_status {
+  HK_OK = 0,
+  HK_ERR_ARG = 1,          /* invalid argument (size, width, pointer)            */
+  HK_ERR_NOMEM = 2,        /* device allocation failed                           */
+  HK_ERR_CUDA = 3,         /* a CUDA runtime call failed                         */
+  HK_ERR_ORDER = 4,        /* call out of order (moments -> ldlt -> inv_block ->
+                              lambda1 -> lambda1_grad)                           */
+  HK_ERR_NOT_PD = 5,       /* a pivot d_i <= 0: the truncated matrix is not
+                              positive definite at this precision (Sec. 4.3,
+                              footnote: exact H_N needs no pivoting)            */
+  HK_ERR_PRECISION = 6,    /* working precision too low for the result asked   */
+  HK_ERR_TIMEOUT = 7,      /* a bounded device wait gave up                      */
+  HK_ERR_UNSUPPORTED = 8   /* beta or width not supported by this build          */
+} hk_status;
+
+/* what hk_export reads */
+typedef enum hk_what {
+  HK_MU = 0,      /* moments mu_0..mu_{2N-2}                                     */
+  HK_FACTOR = 1,  /* packed lower triangle, column major: column c holds rows
+                     c..N-1 at offset c*N - c(c-1)/2; diagonal = D, below = L   */
+  HK_D = 2,       /* pivots D_0..D_{N-1}                                         */
+  HK_X = 3,       /* first k columns of L^{-1}, row major N x k                   */
+  HK_S = 4,       /* k x k top-left block of H_N^{-1}, row major                   */
+  HK_EVEC = 5     /* eigenvector of S for its largest eigenvalue (k entries)      */
+} hk_what;
+
+/* Widths compiled into this library: writes up to cap entries of bits values
+ * into out and returns how many there are. */
+HK_API int hk_supported_bits(int* out, int cap);
+
+/* Create a context on CUDA device `device`, ordering work on `cuda_stream`
+ * (a cudaStream_t, borrowed; NULL = legacy default stream). */
+HK_API hk_status hk_create(int device, void* cuda_stream, hk_ctx** out);
+HK_API void hk_destroy(hk_ctx* ctx);
+/* Human-readable description of the context's first error ("" if none). */
+HK_API const char* hk_last_error(const hk_ctx* ctx);
+
+/* a1. Moments mu_j = Gamma((j+1)/beta)/beta, j = 0..2N-2, truncated to `bits`
+ * (Sec. 2, eq. "moments").  beta = beta_num/beta_den, an exact rational.  This
+ * build computes them on the device for beta = 1/m (m >= 1 an integer), where
+ * they are the integers m * (m(j+1)-1)!  (beta = 1/2: 2 (2j+1)!; beta = 1: j!),
+ * formed exactly and truncated once.  Any other beta returns
+ * HK_ERR_UNSUPPORTED: import the moments with hk_set_moments instead. */
+HK_API hk_status hk_moments(hk_ctx* ctx, int64_t beta_num, int64_t beta_den, int N, int bits);
+
+/* a1'. Import 2N-1 moments (host arrays, number layout above) for any weight;
+ * beta_num/beta_den is recorded for hk_lambda1_grad (0/0 = unknown). */
+HK_API hk_status hk_set_moments(hk_ctx* ctx, int N, int bits, const int32_t* sign, const int32_t* exp,
+                                const uint32_t* limbs, int64_t beta_num, int64_t beta_den);
+
+/* a2-a4. LDL^T of H_N in place by Algorithm 1 (Sec. 4.3): for each column i,
+ * B_i[r] = trunc(A[r][i] / A[i][i]) (exactly truncated quotient), then
+ * A[r][c] = trunc(A[r][c] - A[c][i] * B_i[r]) for i < c <= r, one rounding per
+ * update.  No pivoting.  Enqueues only; a non-positive pivot is reported as
+ * HK_ERR_NOT_PD by the next synchronising call. */
+HK_API hk_status hk_ldlt(hk_ctx* ctx);
+
+/* a5-a6. X = first k columns of L^{-1} by Algorithm 4 (Sec. 4.4; row
+ * elimination, updates in increasing pivot order, one rounding each), then
+ * S = (H_N^{-1})[0:k, 0:k], S_ab = sum_l X[l][a] X[l][b] / D_l (Sec. 4.4 eq.
+ * "index", Sec. 4.5), each term and partial sum truncated to the working
+ * precision.  1 <= k <= min(N, 64). */
+HK_API hk_status hk_inv_block(hk_ctx* ctx, int k);
+
+/* a7. The n_eig (1..3) largest eigenvalues nu_m of S and lambda_m = 1/nu_m
+ * (Sec. 4.2), with the truncation estimate lambda_m(k) - lambda_m(k-1) from the
+ * leading (k-1) x (k-1) block (Sec. 4.5, Table 2).  Outputs (host, any may be
+ * NULL): lambda in the number layout (n_eig numbers), lambda_f64[n_eig],
+ * trunc_err_f64[n_eig] (NaN when k == 1).  Synchronises. */
+HK_API hk_status hk_lambda1(hk_ctx* ctx, int n_eig, int32_t* sign, int32_t* exp, uint32_t* limbs,
+                            double* lambda_f64, double* trunc_err_f64);
+
+/* a8. d lambda_1 / d beta of the block estimate lambda_1 = 1/nu_1:
+ * (w^T Hdot w)/nu_1^2 with w = L^{-T} D^{-1} X u (u the unit eigenvector) and
+ * Hdot_ij = d mu_{i+j}/d beta = -(mu/beta)(1 + x psi(x)), x = (i+j+1)/beta.
+ * Needs beta = 1/m.  Outputs (host, may be NULL): one number, and its double.
+ * Synchronises. */
+HK_API hk_status hk_lambda1_grad(hk_ctx* ctx, int32_t* sign, int32_t* exp, uint32_t* limbs, double* f64);
+
+/* Copy count numbers starting at index first of `what` to host arrays.
+ * Synchronises. */
+HK_API hk_status hk_export(hk_ctx* ctx, int what, int64_t first, int64_t count, int32_t* sign, int32_t* exp,
+                           uint32_t* limbs);
+
+/* Elementwise primitives on caller-owned DEVICE arrays of `count` numbers of
+ * width `bits`, ordered on cuda_stream (no synchronisation):
+ *   hk_fused_batch: out[i] = trunc(a[i] - x[i]*y[i])  (the update of Alg. 1/4)
+ *   hk_div_batch:   out[i] = trunc(a[i] / d[i])      (d[i] != 0)
+ * `out` may not alias the inputs. */
+HK_API hk_status hk_fused_batch(int bits, int64_t count, const int32_t* a_sign, const int32_t* a_exp,
+                                const uint32_t* a_limbs, const int32_t* x_sign, const int32_t* x_exp,
+                                const uint32_t* x_limbs, const int32_t* y_sign, const int32_t* y_exp,
+                                const uint32_t* y_limbs, int32_t* out_sign, int32_t* out_exp,
+                                uint32_t* out_limbs, void* cuda_stream);
+HK_API hk_status hk_div_batch(int bits, int64_t count, const int32_t* a_sign, const int32_t* a_exp,
+                              const uint32_t* a_limbs, const int32_t* d_sign, const int32_t* d_exp,
+                              const uint32_t* d_limbs, int32_t* out_sign, int32_t* out_exp, uint32_t* out_limbs,
+                              void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HK_H */

@@ -1,0 +1,241 @@
+"""Python binding of libhk (include/hk.h): argument marshalling only.
+
+Every step of the path runs in the CUDA library; this module loads
+``_build/libhk.so`` (built by ``build.build()``), forwards calls with the same
+names as the C ABI, and converts the (sign, exp, limbs) layout to and from
+numpy arrays.  There is no CPU fallback: if the library is missing the first
+call raises.
+
+Number layout: value = (-1)^sign * (sum_k limbs[k] 2^(32k)) * 2^(32*exp), n limbs
+little endian with a non-zero top limb, or all zero for 0.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhk.so")
+
+HK_OK, HK_ERR_ARG, HK_ERR_NOMEM, HK_ERR_CUDA, HK_ERR_ORDER = 0, 1, 2, 3, 4
+HK_ERR_NOT_PD, HK_ERR_PRECISION, HK_ERR_TIMEOUT, HK_ERR_UNSUPPORTED = 5, 6, 7, 8
+HK_MU, HK_FACTOR, HK_D, HK_X, HK_S, HK_EVEC = 0, 1, 2, 3, 4, 5
+
+STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA", 4: "HK_ERR_ORDER",
+                5: "HK_ERR_NOT_PD", 6: "HK_ERR_PRECISION", 7: "HK_ERR_TIMEOUT", 8: "HK_ERR_UNSUPPORTED"}
+
+# every entry point declared in include/hk.h
+EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
+           "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
+           "hk_div_batch"]
+
+
+class HKError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_U32P = ctypes.POINTER(ctypes.c_uint32)
+_F64P = ctypes.POINTER(ctypes.c_double)
+
+
+def load(path=LIB_PATH):
+    """Load libhk.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libhk.so not found at {path}: call paper_1810_01478_gb300.build.build() first")
+    L = ctypes.CDLL(path)
+    L.hk_supported_bits.argtypes = [_I32P, ctypes.c_int]
+    L.hk_supported_bits.restype = ctypes.c_int
+    L.hk_create.argtypes = [ctypes.c_int, _P, ctypes.POINTER(_P)]
+    L.hk_destroy.argtypes = [_P]
+    L.hk_destroy.restype = None
+    L.hk_last_error.argtypes = [_P]
+    L.hk_last_error.restype = ctypes.c_char_p
+    L.hk_moments.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
+    L.hk_set_moments.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I32P, _I32P, _U32P, ctypes.c_int64,
+                                 ctypes.c_int64]
+    L.hk_ldlt.argtypes = [_P]
+    L.hk_inv_block.argtypes = [_P, ctypes.c_int]
+    L.hk_lambda1.argtypes = [_P, ctypes.c_int, _I32P, _I32P, _U32P, _F64P, _F64P]
+    L.hk_lambda1_grad.argtypes = [_P, _I32P, _I32P, _U32P, _F64P]
+    L.hk_export.argtypes = [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _I32P, _I32P, _U32P]
+    L.hk_fused_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 12 + [_P]
+    L.hk_div_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 9 + [_P]
+    for name in ("hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
+                 "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _check(st, ctx=None, what=""):
+    if st != HK_OK:
+        msg = load().hk_last_error(ctx).decode() if ctx else what
+        raise HKError(st, msg or what)
+
+
+def hk_supported_bits():
+    L = load()
+    cnt = L.hk_supported_bits(None, 0)
+    out = np.zeros(cnt, np.int32)
+    L.hk_supported_bits(_ptr(out, ctypes.c_int32), cnt)
+    return [int(v) for v in out]
+
+
+def hk_create(device=0, stream=None):
+    """stream: a cudaStream_t as an int (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+    L = load()
+    h = _P()
+    _check(L.hk_create(device, _P(stream or 0), ctypes.byref(h)), what="hk_create")
+    return h
+
+
+def hk_destroy(ctx):
+    load().hk_destroy(ctx)
+
+
+def hk_last_error(ctx):
+    return load().hk_last_error(ctx).decode()
+
+
+def hk_moments(ctx, beta_num, beta_den, N, bits):
+    _check(load().hk_moments(ctx, beta_num, beta_den, N, bits), ctx)
+
+
+def hk_set_moments(ctx, N, bits, sign, exp, limbs, beta_num=0, beta_den=0):
+    sign = np.ascontiguousarray(sign, np.int32)
+    exp = np.ascontiguousarray(exp, np.int32)
+    limbs = np.ascontiguousarray(limbs, np.uint32)
+    n = bits // 32
+    if sign.size != 2 * N - 1 or exp.size != 2 * N - 1 or limbs.size != (2 * N - 1) * n:
+        raise ValueError("hk_set_moments needs 2N-1 numbers of bits/32 limbs")
+    _check(load().hk_set_moments(ctx, N, bits, _ptr(sign, ctypes.c_int32), _ptr(exp, ctypes.c_int32),
+                                 _ptr(limbs, ctypes.c_uint32), beta_num, beta_den), ctx)
+
+
+def hk_ldlt(ctx):
+    _check(load().hk_ldlt(ctx), ctx)
+
+
+def hk_inv_block(ctx, k):
+    _check(load().hk_inv_block(ctx, k), ctx)
+
+
+def hk_lambda1(ctx, n_eig, n):
+    """Returns (sign[n_eig], exp[n_eig], limbs[n_eig, n], lambda_f64[n_eig], trunc_err_f64[n_eig])."""
+    s = np.zeros(n_eig, np.int32)
+    e = np.zeros(n_eig, np.int32)
+    m = np.zeros((n_eig, n), np.uint32)
+    f = np.zeros(n_eig, np.float64)
+    t = np.zeros(n_eig, np.float64)
+    _check(load().hk_lambda1(ctx, n_eig, _ptr(s, ctypes.c_int32), _ptr(e, ctypes.c_int32),
+                             _ptr(m, ctypes.c_uint32), _ptr(f, ctypes.c_double), _ptr(t, ctypes.c_double)), ctx)
+    return s, e, m, f, t
+
+
+def hk_lambda1_grad(ctx, n):
+    s = np.zeros(1, np.int32)
+    e = np.zeros(1, np.int32)
+    m = np.zeros((1, n), np.uint32)
+    f = np.zeros(1, np.float64)
+    _check(load().hk_lambda1_grad(ctx, _ptr(s, ctypes.c_int32), _ptr(e, ctypes.c_int32),
+                                  _ptr(m, ctypes.c_uint32), _ptr(f, ctypes.c_double)), ctx)
+    return s, e, m, f
+
+
+def hk_export(ctx, what, first, count, n):
+    s = np.zeros(count, np.int32)
+    e = np.zeros(count, np.int32)
+    m = np.zeros((count, n), np.uint32)
+    _check(load().hk_export(ctx, what, first, count, _ptr(s, ctypes.c_int32), _ptr(e, ctypes.c_int32),
+                            _ptr(m, ctypes.c_uint32)), ctx)
+    return s, e, m
+
+
+def hk_fused_batch(bits, count, a, x, y, out, stream=None):
+    """a, x, y, out: (sign_ptr, exp_ptr, limbs_ptr) device addresses (ints)."""
+    args = [_P(p) for t in (a, x, y, out) for p in t]
+    _check(load().hk_fused_batch(bits, count, *args, _P(stream or 0)), what="hk_fused_batch")
+
+
+def hk_div_batch(bits, count, a, d, out, stream=None):
+    args = [_P(p) for t in (a, d, out) for p in t]
+    _check(load().hk_div_batch(bits, count, *args, _P(stream or 0)), what="hk_div_batch")
+
+
+# --- layout helpers (host-side marshalling) ---------------------------------
+
+def limbs_to_int(row):
+    v = 0
+    for i, w in enumerate(np.asarray(row, np.uint64).tolist()):
+        v |= int(w) << (32 * i)
+    return v
+
+
+def int_to_limbs(v, n):
+    return np.array([(v >> (32 * i)) & 0xFFFFFFFF for i in range(n)], np.uint32)
+
+
+def int_to_layout(v, n):
+    """An exact integer truncated into the number layout (sign, exp, limbs)."""
+    if v == 0:
+        return 0, 0, np.zeros(n, np.uint32)
+    s = 1 if v < 0 else 0
+    a = -v if v < 0 else v
+    L = (a.bit_length() + 31) // 32
+    e = L - n
+    a = a >> (32 * e) if e >= 0 else a << (32 * -e)
+    return s, e, int_to_limbs(a, n)
+
+
+class Hankel:
+    """The whole path on one device: moments -> LDL^T -> block -> lambda (-> gradient)."""
+
+    def __init__(self, device=0, stream=None):
+        self.ctx = hk_create(device, stream)
+        self.n = None
+
+    def close(self):
+        if self.ctx is not None:
+            hk_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def moments(self, beta_num, beta_den, N, bits):
+        self.n = bits // 32
+        hk_moments(self.ctx, beta_num, beta_den, N, bits)
+
+    def set_moments(self, N, bits, sign, exp, limbs, beta_num=0, beta_den=0):
+        self.n = bits // 32
+        hk_set_moments(self.ctx, N, bits, sign, exp, limbs, beta_num, beta_den)
+
+    def ldlt(self):
+        hk_ldlt(self.ctx)
+
+    def inv_block(self, k):
+        hk_inv_block(self.ctx, k)
+
+    def lambda1(self, n_eig=1):
+        return hk_lambda1(self.ctx, n_eig, self.n)
+
+    def lambda1_grad(self):
+        return hk_lambda1_grad(self.ctx, self.n)
+
+    def export(self, what, first, count):
+        return hk_export(self.ctx, what, first, count, self.n)

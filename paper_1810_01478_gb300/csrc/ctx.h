@@ -1,0 +1,65 @@
+// Host-side context of libhk (one factorisation problem on one device).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hk.h"
+#include "common.cuh"
+
+namespace hk {
+
+// A device array of `count` numbers of n limbs each (owned).
+struct DevVec {
+  int64_t count = 0;
+  int n = 0;
+  int32_t* sgn = nullptr;
+  int32_t* exp = nullptr;
+  uint32_t* mant = nullptr;
+  MPVec view() const { return MPVec{sgn, exp, mant}; }
+  MPVec at(int64_t i) const { return MPVec{sgn + i, exp + i, mant + i * n}; }
+};
+
+cudaError_t dev_alloc(DevVec& v, int64_t count, int n);
+void dev_free(DevVec& v);
+
+enum Stage { ST_NONE = 0, ST_MOMENTS = 1, ST_LDLT = 2, ST_INVBLOCK = 3, ST_LAMBDA = 4 };
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  hk_status sticky = HK_OK;
+  int stage = ST_NONE;
+  int N = 0, bits = 0, n = 0, M = 0, k = 0;
+  int64_t beta_num = 0, beta_den = 0;
+  int* d_err = nullptr;       // device error flags (ErrBits)
+  DevVec mu, A, U, X, S, evec, scratch;
+  uint32_t* rec = nullptr;    // pivot reciprocal scratch (n limbs)
+  int* rec_meta = nullptr;
+  // eigen results (host copies, filled by the lambda stage)
+  int n_eig = 0;
+  std::vector<int32_t> lam_sgn, lam_exp;
+  std::vector<uint32_t> lam_mant;
+  std::vector<double> lam_f64, trunc_f64;
+};
+
+hk_status set_error(Ctx& c, hk_status s, const std::string& msg);
+hk_status check_cuda(Ctx& c, cudaError_t e, const char* what);
+hk_status read_device_flags(Ctx& c);  // synchronises
+
+// Per-width operations, one instantiation per limb count M (= n/32).
+struct OpsTable {
+  int M;
+  hk_status (*ldlt)(Ctx&);
+  hk_status (*inv_block)(Ctx&);
+  hk_status (*lambda)(Ctx&, int n_eig);
+  hk_status (*grad)(Ctx&, int32_t* sgn, int32_t* exp, uint32_t* mant, double* f64);
+  cudaError_t (*fused_batch)(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count, cudaStream_t s);
+  cudaError_t (*div_batch)(MPVec a, MPVec d, MPVec out, int64_t count, int* err, cudaStream_t s);
+};
+
+const OpsTable* ops_for(int M);
+
+}  // namespace hk

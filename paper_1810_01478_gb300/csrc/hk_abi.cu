@@ -1,0 +1,339 @@
+// The C ABI of libhk (declared in include/hk.h): context management, call-order
+// enforcement, host <-> device transfers and dispatch to the per-width launchers.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+#include "k_moments.cuh"
+#include "widths.h"
+
+namespace hk {
+
+#define HK_DECL(m) const OpsTable* ops_m##m();
+HK_FOR_EACH_M(HK_DECL)
+#undef HK_DECL
+
+const OpsTable* ops_for(int M) {
+#define HK_CASE(m) \
+  if (M == m) return ops_m##m();
+  HK_FOR_EACH_M(HK_CASE)
+#undef HK_CASE
+  return nullptr;
+}
+
+cudaError_t dev_alloc(DevVec& v, int64_t count, int n) {
+  v.count = count;
+  v.n = n;
+  cudaError_t e;
+  const int64_t c = count > 0 ? count : 1;
+  if ((e = cudaMalloc(&v.sgn, c * 4)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&v.exp, c * 4)) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&v.mant, c * (int64_t)n * 4)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+void dev_free(DevVec& v) {
+  if (v.sgn) cudaFree(v.sgn);
+  if (v.exp) cudaFree(v.exp);
+  if (v.mant) cudaFree(v.mant);
+  v = DevVec{};
+}
+
+hk_status set_error(Ctx& c, hk_status s, const std::string& msg) {
+  if (c.sticky == HK_OK) {
+    c.sticky = s;
+    c.err = msg;
+  }
+  return s;
+}
+
+hk_status check_cuda(Ctx& c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return HK_OK;
+  const hk_status s = (e == cudaErrorMemoryAllocation) ? HK_ERR_NOMEM : HK_ERR_CUDA;
+  return set_error(c, s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+hk_status read_device_flags(Ctx& c) {
+  hk_status st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising");
+  if (st != HK_OK) return st;
+  int flags = 0;
+  st = check_cuda(c, cudaMemcpy(&flags, c.d_err, sizeof(int), cudaMemcpyDeviceToHost), "reading device flags");
+  if (st != HK_OK) return st;
+  if (flags & ERR_NOT_PD)
+    return set_error(c, HK_ERR_NOT_PD, "a pivot d_i <= 0: raise the working precision");
+  if (flags & ERR_PRECISION) return set_error(c, HK_ERR_PRECISION, "working precision too low");
+  if (flags & ERR_LOOP) return set_error(c, HK_ERR_CUDA, "internal correction loop exceeded its bound");
+  if (flags & ERR_ARG) return set_error(c, HK_ERR_ARG, "invalid device operand (zero divisor or capacity)");
+  return HK_OK;
+}
+
+}  // namespace hk
+
+using namespace hk;
+
+struct hk_ctx {
+  Ctx c;
+};
+
+static bool valid_bits(int bits) { return bits > 0 && bits % 1024 == 0 && ops_for(bits / 1024) != nullptr; }
+
+static hk_status enter(hk_ctx* h) {
+  if (!h) return HK_ERR_ARG;
+  if (h->c.sticky != HK_OK) return h->c.sticky;
+  return check_cuda(h->c, cudaSetDevice(h->c.device), "cudaSetDevice");
+}
+
+extern "C" {
+
+int hk_supported_bits(int* out, int cap) {
+  int cnt = 0;
+#define HK_LIST(m)                      \
+  if (out && cnt < cap) out[cnt] = 1024 * m; \
+  ++cnt;
+  HK_FOR_EACH_M(HK_LIST)
+#undef HK_LIST
+  return cnt;
+}
+
+hk_status hk_create(int device, void* cuda_stream, hk_ctx** out) {
+  if (!out) return HK_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return HK_ERR_CUDA;
+  hk_ctx* h = new (std::nothrow) hk_ctx();
+  if (!h) return HK_ERR_NOMEM;
+  h->c.device = device;
+  h->c.stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&h->c.d_err, 64) != cudaSuccess ||
+      cudaMemsetAsync(h->c.d_err, 0, 64, h->c.stream) != cudaSuccess) {
+    if (h->c.d_err) cudaFree(h->c.d_err);
+    delete h;
+    return HK_ERR_CUDA;
+  }
+  *out = h;
+  return HK_OK;
+}
+
+void hk_destroy(hk_ctx* h) {
+  if (!h) return;
+  cudaSetDevice(h->c.device);
+  cudaStreamSynchronize(h->c.stream);
+  Ctx& c = h->c;
+  dev_free(c.mu);
+  dev_free(c.A);
+  dev_free(c.U);
+  dev_free(c.X);
+  dev_free(c.S);
+  dev_free(c.evec);
+  dev_free(c.scratch);
+  if (c.rec) cudaFree(c.rec);
+  if (c.d_err) cudaFree(c.d_err);
+  delete h;
+}
+
+const char* hk_last_error(const hk_ctx* h) { return h ? h->c.err.c_str() : "null context"; }
+
+static hk_status begin_moments(hk_ctx* h, int N, int bits) {
+  Ctx& c = h->c;
+  if (N < 1 || N > (1 << 20)) return set_error(c, HK_ERR_ARG, "N out of range");
+  if (!valid_bits(bits)) return set_error(c, HK_ERR_UNSUPPORTED, "bits must be 1024*M for a compiled M");
+  c.N = N;
+  c.bits = bits;
+  c.n = bits / 32;
+  c.M = bits / 1024;
+  c.k = 0;
+  c.stage = ST_NONE;
+  if (c.mu.count != 2 * N - 1 || c.mu.n != c.n) {
+    dev_free(c.mu);
+    hk_status st = check_cuda(c, dev_alloc(c.mu, 2 * N - 1, c.n), "allocating moments");
+    if (st != HK_OK) return st;
+  }
+  return check_cuda(c, cudaMemsetAsync(c.d_err, 0, 64, c.stream), "clearing flags");
+}
+
+hk_status hk_moments(hk_ctx* h, int64_t beta_num, int64_t beta_den, int N, int bits) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (beta_num <= 0 || beta_den <= 0) return set_error(c, HK_ERR_ARG, "beta must be positive");
+  if (beta_den % beta_num != 0)
+    return set_error(c, HK_ERR_UNSUPPORTED, "device moments need beta = 1/m; use hk_set_moments");
+  const int64_t m = beta_den / beta_num;
+  if (m > 64) return set_error(c, HK_ERR_UNSUPPORTED, "beta = 1/m with m > 64");
+  if ((st = begin_moments(h, N, bits)) != HK_OK) return st;
+  // limbs of G_{2N-2} = m * (m(2N-1) - 1)!
+  const double top = (double)m * (2.0 * N - 1.0);
+  const double bits_needed = (std::lgamma(top) + std::log((double)m)) / std::log(2.0) + 96.0;
+  int64_t cap = ((int64_t)(bits_needed / 32.0) + 2 + 31) / 32 * 32;
+  if (cap < 64) cap = 64;
+  if (cap * 4 > 200 * 1024) return set_error(c, HK_ERR_UNSUPPORTED, "moments too long for the exact kernel");
+  if ((st = check_cuda(c, cudaFuncSetAttribute(k_moments_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(cap * 4)),
+                       "smem attribute")) != HK_OK)
+    return st;
+  k_moments_exact<<<1, 32, cap * 4, c.stream>>>((int)m, N, c.n, (int)cap, c.mu.view(), c.d_err);
+  if ((st = check_cuda(c, cudaGetLastError(), "launching the moments")) != HK_OK) return st;
+  c.beta_num = beta_num;
+  c.beta_den = beta_den;
+  c.stage = ST_MOMENTS;
+  return HK_OK;
+}
+
+hk_status hk_set_moments(hk_ctx* h, int N, int bits, const int32_t* sign, const int32_t* exp,
+                         const uint32_t* limbs, int64_t beta_num, int64_t beta_den) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (!sign || !exp || !limbs) return set_error(c, HK_ERR_ARG, "null host array");
+  if ((st = begin_moments(h, N, bits)) != HK_OK) return st;
+  const int64_t cnt = 2 * (int64_t)N - 1;
+  if ((st = check_cuda(c, cudaMemcpyAsync(c.mu.sgn, sign, cnt * 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+      (st = check_cuda(c, cudaMemcpyAsync(c.mu.exp, exp, cnt * 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+      (st = check_cuda(c, cudaMemcpyAsync(c.mu.mant, limbs, cnt * c.n * 4, cudaMemcpyHostToDevice, c.stream),
+                       "H2D")))
+    return st;
+  // the copies read pageable host memory: finish them before returning
+  if ((st = check_cuda(c, cudaStreamSynchronize(c.stream), "H2D sync")) != HK_OK) return st;
+  c.beta_num = beta_num;
+  c.beta_den = beta_den;
+  c.stage = ST_MOMENTS;
+  return HK_OK;
+}
+
+hk_status hk_ldlt(hk_ctx* h) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_ldlt before the moments");
+  st = ops_for(c.M)->ldlt(c);
+  if (st == HK_OK) c.stage = ST_LDLT;
+  return st;
+}
+
+hk_status hk_inv_block(hk_ctx* h, int k) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (c.stage < ST_LDLT) return set_error(c, HK_ERR_ORDER, "hk_inv_block before hk_ldlt");
+  if (k < 1 || k > c.N || k > 64) return set_error(c, HK_ERR_ARG, "k must be in 1..min(N, 64)");
+  c.k = k;
+  st = ops_for(c.M)->inv_block(c);
+  if (st == HK_OK) c.stage = ST_INVBLOCK;
+  return st;
+}
+
+hk_status hk_lambda1(hk_ctx* h, int n_eig, int32_t* sign, int32_t* exp, uint32_t* limbs, double* lambda_f64,
+                     double* trunc_err_f64) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (c.stage < ST_INVBLOCK) return set_error(c, HK_ERR_ORDER, "hk_lambda1 before hk_inv_block");
+  if (n_eig < 1 || n_eig > 3 || n_eig > c.k) return set_error(c, HK_ERR_ARG, "n_eig must be in 1..min(3, k)");
+  if ((st = ops_for(c.M)->lambda(c, n_eig)) != HK_OK) return st;
+  if ((st = read_device_flags(c)) != HK_OK) return st;
+  for (int m = 0; m < n_eig; ++m) {
+    if (sign) sign[m] = c.lam_sgn[m];
+    if (exp) exp[m] = c.lam_exp[m];
+    if (limbs) std::memcpy(limbs + (size_t)m * c.n, c.lam_mant.data() + (size_t)m * c.n, (size_t)c.n * 4);
+    if (lambda_f64) lambda_f64[m] = c.lam_f64[m];
+    if (trunc_err_f64) trunc_err_f64[m] = c.trunc_f64[m];
+  }
+  c.stage = ST_LAMBDA;
+  return HK_OK;
+}
+
+hk_status hk_lambda1_grad(hk_ctx* h, int32_t* sign, int32_t* exp, uint32_t* limbs, double* f64) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (c.stage < ST_LAMBDA) return set_error(c, HK_ERR_ORDER, "hk_lambda1_grad before hk_lambda1");
+  if (c.beta_den <= 0 || c.beta_num <= 0 || c.beta_den % c.beta_num != 0)
+    return set_error(c, HK_ERR_UNSUPPORTED, "the gradient needs beta = 1/m");
+  if ((st = ops_for(c.M)->grad(c, sign, exp, limbs, f64)) != HK_OK) return st;
+  return read_device_flags(c);
+}
+
+hk_status hk_export(hk_ctx* h, int what, int64_t first, int64_t count, int32_t* sign, int32_t* exp,
+                    uint32_t* limbs) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  const DevVec* v = nullptr;
+  int64_t base = 0, total = 0;
+  switch (what) {
+    case HK_MU: if (c.stage >= ST_MOMENTS) { v = &c.mu; total = 2 * (int64_t)c.N - 1; } break;
+    case HK_FACTOR: if (c.stage >= ST_LDLT) { v = &c.A; total = (int64_t)c.N * (c.N + 1) / 2; } break;
+    case HK_D:
+      if (c.stage >= ST_LDLT) { v = &c.A; total = c.N; }
+      break;
+    case HK_X: if (c.stage >= ST_INVBLOCK) { v = &c.X; total = (int64_t)c.N * c.k; } break;
+    case HK_S: if (c.stage >= ST_INVBLOCK) { v = &c.S; total = (int64_t)c.k * c.k; } break;
+    case HK_EVEC: if (c.stage >= ST_LAMBDA) { v = &c.evec; total = c.k; } break;
+    default: return set_error(c, HK_ERR_ARG, "unknown export");
+  }
+  if (!v) return set_error(c, HK_ERR_ORDER, "export of a stage not yet computed");
+  if (first < 0 || count < 0 || first + count > total) return set_error(c, HK_ERR_ARG, "export range");
+  if ((st = read_device_flags(c)) != HK_OK) return st;
+  auto copy = [&](int64_t dst, int64_t src, int64_t cnt) -> hk_status {
+    hk_status s2 = HK_OK;
+    if (sign && (s2 = check_cuda(c, cudaMemcpy(sign + dst, v->sgn + src, cnt * 4, cudaMemcpyDeviceToHost), "D2H")))
+      return s2;
+    if (exp && (s2 = check_cuda(c, cudaMemcpy(exp + dst, v->exp + src, cnt * 4, cudaMemcpyDeviceToHost), "D2H")))
+      return s2;
+    if (limbs && (s2 = check_cuda(c, cudaMemcpy(limbs + dst * c.n, v->mant + src * c.n, cnt * c.n * 4,
+                                                cudaMemcpyDeviceToHost), "D2H")))
+      return s2;
+    return HK_OK;
+  };
+  if (what == HK_D) {  // the pivots sit on the diagonal of the packed factor
+    for (int64_t i = 0; i < count; ++i)
+      if ((st = copy(i, tri_pos(c.N, first + i, first + i), 1)) != HK_OK) return st;
+    return HK_OK;
+  }
+  return count ? copy(0, base + first, count) : HK_OK;
+}
+
+static MPVec cvec(const int32_t* s, const int32_t* e, const uint32_t* m) {
+  return MPVec{const_cast<int32_t*>(s), const_cast<int32_t*>(e), const_cast<uint32_t*>(m)};
+}
+
+hk_status hk_fused_batch(int bits, int64_t count, const int32_t* a_sign, const int32_t* a_exp,
+                         const uint32_t* a_limbs, const int32_t* x_sign, const int32_t* x_exp,
+                         const uint32_t* x_limbs, const int32_t* y_sign, const int32_t* y_exp,
+                         const uint32_t* y_limbs, int32_t* out_sign, int32_t* out_exp, uint32_t* out_limbs,
+                         void* cuda_stream) {
+  if (!valid_bits(bits) || count < 0) return HK_ERR_ARG;
+  if (count == 0) return HK_OK;
+  if (!a_sign || !a_exp || !a_limbs || !x_sign || !x_exp || !x_limbs || !y_sign || !y_exp || !y_limbs ||
+      !out_sign || !out_exp || !out_limbs)
+    return HK_ERR_ARG;
+  const cudaError_t e = ops_for(bits / 1024)->fused_batch(
+      cvec(a_sign, a_exp, a_limbs), cvec(x_sign, x_exp, x_limbs), cvec(y_sign, y_exp, y_limbs),
+      MPVec{out_sign, out_exp, out_limbs}, count, static_cast<cudaStream_t>(cuda_stream));
+  return e == cudaSuccess ? HK_OK : HK_ERR_CUDA;
+}
+
+hk_status hk_div_batch(int bits, int64_t count, const int32_t* a_sign, const int32_t* a_exp,
+                       const uint32_t* a_limbs, const int32_t* d_sign, const int32_t* d_exp,
+                       const uint32_t* d_limbs, int32_t* out_sign, int32_t* out_exp, uint32_t* out_limbs,
+                       void* cuda_stream) {
+  if (!valid_bits(bits) || count < 0) return HK_ERR_ARG;
+  if (count == 0) return HK_OK;
+  if (!a_sign || !a_exp || !a_limbs || !d_sign || !d_exp || !d_limbs || !out_sign || !out_exp || !out_limbs)
+    return HK_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int* flag = nullptr;
+  if (cudaMallocAsync(&flag, sizeof(int), s) != cudaSuccess) return HK_ERR_NOMEM;
+  cudaMemsetAsync(flag, 0, sizeof(int), s);
+  cudaError_t e = ops_for(bits / 1024)->div_batch(cvec(a_sign, a_exp, a_limbs), cvec(d_sign, d_exp, d_limbs),
+                                                   MPVec{out_sign, out_exp, out_limbs}, count, flag, s);
+  int host_flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(flag, s);
+  if (e != cudaSuccess) return HK_ERR_CUDA;
+  return host_flag ? HK_ERR_ARG : HK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,238 @@
+// Kernels of the factorisation: elementwise primitives, Hankel assembly,
+// pivot reciprocal, column scale (B_i) and the trailing rank-1 update
+// (Algorithm 1, Sec. 4.3).
+#pragma once
+#include "common.cuh"
+#include "mp_div.cuh"
+
+namespace hk {
+
+template <int M>
+__device__ __forceinline__ void load_hdr(const MPVec& v, int64_t i, int& s, int& e) {
+  s = v.sgn[i];
+  e = v.exp[i];
+}
+
+template <int M>
+__device__ __forceinline__ void store_result(const MPVec& v, int64_t i, const Result& r, const uint32_t (&out)[M]) {
+  constexpr int n = 32 * M;
+  store_chunk<M>(v.mant + i * n, out);
+  if (lane_id() == 0) {
+    v.sgn[i] = r.sgn;
+    v.exp[i] = r.exp;
+  }
+}
+
+// One fused operation out = trunc_n(a - x*y) for a warp; x in registers (xc),
+// y staged in sm.ys, a staged in sm.sa.
+template <int M>
+__device__ __forceinline__ Result fused_staged(const WarpSmem<M>& sm, const uint32_t (&xc)[M], int sx, int ex,
+                                               int sy, int ey, int sa_sgn, int ea, uint32_t (&out)[M]) {
+  constexpr int n = 32 * M;
+  const bool x_zero = __shfl_sync(FULL, xc[M - 1], 31) == 0u;
+  const bool y_zero = sm.ys[n - 1] == 0u;
+  const bool a_zero = sm.sa[n - 1] == 0u;
+  const bool p_zero = x_zero || y_zero;
+  if (!p_zero) {
+    uint32_t lo[M], hi[M];
+    warp_mul<M>(xc, sm.ys, lo, hi);
+    stage_product<M>(sm.sp, lo, hi);
+    __syncwarp();
+  }
+  return sub_product<M>(sm, sa_sgn, ea, a_zero, sx ^ sy, ex + ey, p_zero, out);
+}
+
+// ---------------------------------------------------------------------------
+// elementwise primitives (used by the format tests and exported as-is)
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_fused_batch(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  WarpSmem<M> sm(smem + wib * WarpSmem<M>::words);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; e < count; e += nw) {
+    copy_to_smem<M>(sm.ys, y.mant + e * n);
+    copy_to_smem<M>(sm.sa, a.mant + e * n);
+    uint32_t xc[M];
+    load_chunk<M>(x.mant + e * n, xc);
+    __syncwarp();
+    uint32_t o[M];
+    const Result r = fused_staged<M>(sm, xc, x.sgn[e], x.exp[e], y.sgn[e], y.exp[e], a.sgn[e], a.exp[e], o);
+    store_result<M>(out, e, r, o);
+    __syncwarp();
+  }
+}
+
+// out = trunc_n(a / d), each warp forming its own reciprocal (test primitive).
+template <int M>
+__global__ void k_div_batch(MPVec a, MPVec d, MPVec out, int64_t count, int* err) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* ys = smem + wib * (4 * n + 4);
+  uint32_t* yt = ys + n;
+  uint32_t* sp = yt + n;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; e < count; e += nw) {
+    uint32_t dc[M], ac[M], R[M], q[M];
+    load_chunk<M>(d.mant + e * n, dc);
+    load_chunk<M>(a.mant + e * n, ac);
+    const bool d_zero = __shfl_sync(FULL, dc[M - 1], 31) == 0u;
+    const bool a_zero = __shfl_sync(FULL, ac[M - 1], 31) == 0u;
+    if (d_zero || a_zero) {
+      if (d_zero && lane_id() == 0) atomicOr(err, ERR_ARG);
+#pragma unroll
+      for (int k = 0; k < M; ++k) q[k] = 0;
+      Result r{0, 0, true};
+      store_result<M>(out, e, r, q);
+      continue;
+    }
+    int sh, t;
+    warp_recip<M>(dc, ys, sp, R, sh, err);
+#pragma unroll
+    for (int k = 0; k < M; ++k) ys[lane_id() * M + k] = R[k];
+    __syncwarp();
+    warp_quot<M>(ac, dc, ys, sh, yt, sp, q, t, err);
+    Result r;
+    r.zero = false;
+    r.sgn = a.sgn[e] ^ d.sgn[e];
+    r.exp = a.exp[e] - d.exp[e] - t;
+    store_result<M>(out, e, r, q);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Hankel assembly: A[r][c] = mu_{r+c} (packed lower triangle)
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_assemble(MPVec mu, MPVec A, int N) {
+  constexpr int n = 32 * M;
+  const int64_t total = (int64_t)N * (N + 1) / 2;
+  const int64_t q4 = n / 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total * q4; g += stride) {
+    const int64_t pos = g / q4, w = g % q4;
+    // column of pos: largest c with tri_pos(N, c, c) <= pos
+    int64_t c = trail_col(N, pos);
+    const int64_t r = c + (pos - trail_off(N, c));
+    const int64_t s = r + c;
+    reinterpret_cast<uint4*>(A.mant + pos * n)[w] = reinterpret_cast<const uint4*>(mu.mant + s * n)[w];
+    if (w == 0) {
+      A.sgn[pos] = mu.sgn[s];
+      A.exp[pos] = mu.exp[s];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pivot reciprocal (one warp): R_i for d_i = A[i][i]
+// ---------------------------------------------------------------------------
+// rec: n limbs of R, then (sh) in rec_meta[0].
+template <int M>
+__global__ void k_recip_pivot(MPVec A, int N, int i, uint32_t* rec, int* rec_meta, int* err) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  uint32_t* ys = smem;
+  uint32_t* sp = smem + n;
+  const int64_t pos = tri_pos(N, i, i);
+  uint32_t dc[M], R[M];
+  load_chunk<M>(A.mant + pos * n, dc);
+  const bool zero = __shfl_sync(FULL, dc[M - 1], 31) == 0u;
+  if (zero || A.sgn[pos] != 0) {
+    if (lane_id() == 0) atomicOr(err, ERR_NOT_PD);
+    return;
+  }
+  int sh;
+  warp_recip<M>(dc, ys, sp, R, sh, err);
+  store_chunk<M>(rec, R);
+  if (lane_id() == 0) rec_meta[0] = sh;
+}
+
+// ---------------------------------------------------------------------------
+// column scale of step i: U[r] = A[r][i];  A[r][i] = B_i[r] = trunc(A[r][i] / d_i)
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_scale(MPVec A, MPVec U, int N, int i, const uint32_t* rec, const int* rec_meta, int* err) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* ys = smem + wib * (4 * n + 4);
+  uint32_t* yt = ys + n;
+  uint32_t* sp = yt + n;
+  if (*err & ERR_NOT_PD) return;
+  const int64_t dpos = tri_pos(N, i, i);
+  uint32_t dc[M], R[M];
+  load_chunk<M>(A.mant + dpos * n, dc);
+  load_chunk<M>(rec, R);
+  const int sh = rec_meta[0];
+  const int ed = A.exp[dpos];
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = i + 1 + (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; r < N; r += nw) {
+    const int64_t pos = tri_pos(N, r, i);
+    uint32_t ac[M], q[M];
+    load_chunk<M>(A.mant + pos * n, ac);
+    const int sa = A.sgn[pos], ea = A.exp[pos];
+    store_chunk<M>(U.mant + r * n, ac);
+    if (lane_id() == 0) {
+      U.sgn[r] = sa;
+      U.exp[r] = ea;
+    }
+    const bool a_zero = __shfl_sync(FULL, ac[M - 1], 31) == 0u;
+    Result res;
+    if (a_zero) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) q[k] = 0;
+      res = Result{0, 0, true};
+    } else {
+#pragma unroll
+      for (int k = 0; k < M; ++k) ys[lane_id() * M + k] = R[k];
+      __syncwarp();
+      int t;
+      warp_quot<M>(ac, dc, ys, sh, yt, sp, q, t, err);
+      res = Result{sa, ea - ed - t, false};
+    }
+    store_result<M>(A, pos, res, q);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// trailing update of step i (Algorithm 1 inner loops, Sec. 4.3):
+//   A[r][c] = trunc(A[r][c] - U[c] * B_i[r]),  i < c <= r < N
+// U[c] = A[c][i] before scaling (saved by k_scale), B_i[r] = A[r][i] after.
+// One warp per entry; entries enumerated column by column so consecutive
+// warps share U[c].
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(128) k_trailing(MPVec A, MPVec U, int N, int i, int64_t t0, int64_t t1,
+                                                   const int* err) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  WarpSmem<M> sm(smem + wib * WarpSmem<M>::words);
+  if (*err & ERR_NOT_PD) return;
+  const int64_t m = N - 1 - i;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = t0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; t < t1; t += nw) {
+    const int64_t cc = trail_col(m, t);
+    const int64_t c = i + 1 + cc;
+    const int64_t r = c + (t - trail_off(m, cc));
+    const int64_t apos = tri_pos(N, r, c);
+    const int64_t bpos = tri_pos(N, r, i);
+    copy_to_smem<M>(sm.ys, A.mant + bpos * n);
+    copy_to_smem<M>(sm.sa, A.mant + apos * n);
+    uint32_t xc[M];
+    load_chunk<M>(U.mant + c * n, xc);
+    __syncwarp();
+    uint32_t o[M];
+    const Result res = fused_staged<M>(sm, xc, U.sgn[c], U.exp[c], A.sgn[bpos], A.exp[bpos], A.sgn[apos],
+                                       A.exp[apos], o);
+    store_result<M>(A, apos, res, o);
+    __syncwarp();
+  }
+}
+
+}  // namespace hk

@@ -1,0 +1,95 @@
+"""GPU parity of moments and Algorithm 1 (LDL^T) against the oracle, bit for bit."""
+from fractions import Fraction
+
+import pytest
+
+from oracle import mpfloat as F
+from oracle import moments as OM
+from oracle import ldlt as OL
+from tests import inputs
+from tests.layout import from_arrays, to_arrays
+
+pytestmark = pytest.mark.gpu
+
+
+def run_factor(hk, N, bits, beta=(1, 2), mu=None):
+    h = hk.Hankel(0)
+    if mu is None:
+        h.moments(beta[0], beta[1], N, bits)
+    else:
+        s, e, m = to_arrays(mu, bits // 32)
+        h.set_moments(N, bits, s, e, m)
+    h.ldlt()
+    return h
+
+
+def check_factor(h, hk, D, L, N):
+    tri = N * (N + 1) // 2
+    s, e, m = h.export(hk.HK_FACTOR, 0, tri)
+    got = from_arrays(s, e, m)
+    pos = 0
+    bad = []
+    for c in range(N):
+        for r in range(c, N):
+            want = D[c] if r == c else L[r][c]
+            if got[pos] != want:
+                bad.append((r, c))
+            pos += 1
+    assert not bad, f"{len(bad)} entries differ, first {bad[:5]}"
+
+
+@pytest.mark.parametrize("beta,N,bits", [((1, 2), 95, 4096), ((1, 1), 60, 2048), ((1, 3), 40, 1024)])
+def test_moments_bit_exact(beta, N, bits):
+    import paper_1810_01478_gb300 as hk
+    n = bits // 32
+    with hk.Hankel(0) as h:
+        h.moments(beta[0], beta[1], N, bits)
+        got = from_arrays(*h.export(hk.HK_MU, 0, 2 * N - 1))
+    assert got == OM.moments(Fraction(*beta), N, n)
+
+
+@pytest.mark.parametrize("N,bits", [(48, 4096), (1, 4096), (2, 1024), (33, 1024), (20, 24576)])
+def test_ldlt_beta_half_bit_exact(N, bits):
+    import paper_1810_01478_gb300 as hk
+    n = bits // 32
+    mu = OM.moments(Fraction(1, 2), N, n)
+    D, L = OL.ldlt(mu, N, n)
+    h = run_factor(hk, N, bits)
+    try:
+        check_factor(h, hk, D, L, N)
+    finally:
+        h.close()
+
+
+def test_ldlt_beta_one_closed_form_and_oracle():
+    import paper_1810_01478_gb300 as hk
+    N, bits = 40, 2048
+    n = bits // 32
+    mu = OM.moments(Fraction(1), N, n)
+    D, L = OL.ldlt(mu, N, n)
+    with run_factor(hk, N, bits, beta=(1, 1)) as h:
+        check_factor(h, hk, D, L, N)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ldlt_measure_fuzz_bit_exact(seed):
+    import paper_1810_01478_gb300 as hk
+    N, bits = 24, 3072
+    n = bits // 32
+    mu = [F.from_int(v, n) for v in inputs.measure_moments(seed, N)]
+    D, L = OL.ldlt(mu, N, n)
+    with run_factor(hk, N, bits, mu=mu) as h:
+        check_factor(h, hk, D, L, N)
+
+
+def test_not_positive_definite_is_reported():
+    import paper_1810_01478_gb300 as hk
+    N, bits = 3, 1024
+    mu = [F.from_int(v, 32) for v in [2, 3, 5, 9, 17]]  # a 2-atom measure: singular H_3
+    h = run_factor(hk, N, bits, mu=mu)
+    try:
+        with pytest.raises(hk.HKError) as ei:
+            h.export(hk.HK_D, 0, N)
+        assert ei.value.status == hk.HK_ERR_NOT_PD
+    finally:
+        h.close()
