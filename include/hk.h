@@ -133,6 +133,20 @@ HK_API hk_status hk_lambda1_grad(hk_ctx* ctx, int32_t* sign, int32_t* exp, uint3
 HK_API hk_status hk_export(hk_ctx* ctx, int what, int64_t first, int64_t count, int32_t* sign, int32_t* exp,
                            uint32_t* limbs);
 
+/* Profiling (the paper reports per-phase wall times, Table 2; here CUDA
+ * events on the context's stream).  hk_set_profiling(ctx, 1) clears and
+ * enables the counters; hk_get_profile synchronises and writes
+ * HK_PROFILE_FIELDS doubles:
+ *   [0] kernel launches since enabling
+ *   [1] total device time of the trailing-update kernels (Algorithm 1), ms
+ *   [2] number of trailing-update launches
+ *   [3] algorithmic limb products of those launches (n^2 per fused update)
+ *   [4] moments ms, [5] LDL^T ms, [6] Algorithm 4 + block ms,
+ *   [7] eigenvalues ms, [8] gradient ms */
+#define HK_PROFILE_FIELDS 9
+HK_API hk_status hk_set_profiling(hk_ctx* ctx, int on);
+HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
+
 /* Elementwise primitives on caller-owned DEVICE arrays of `count` numbers of
  * width `bits`, ordered on cuda_stream (no synchronisation):
  *   hk_fused_batch: out[i] = trunc(a[i] - x[i]*y[i])  (the update of Alg. 1/4)

@@ -26,6 +26,19 @@ from . import invblock as IB
 from . import eigen as EG
 
 
+def psi(x, mpm):
+    """Digamma at x: for a positive integer x the exact identity
+    psi(x) = H_{x-1} - gamma (harmonic number as an exact Fraction, Euler's
+    gamma from mpmath); otherwise mpmath.digamma."""
+    if isinstance(x, int) or (isinstance(x, Fraction) and x.denominator == 1):
+        x = int(x)
+        h = Fraction(0)
+        for j in range(1, x):
+            h += Fraction(1, j)
+        return mpm.mpf(h.numerator) / h.denominator - mpm.euler
+    return mpm.digamma(x)
+
+
 def analytic_grad(beta, mu_exact, L, D, X, k, n):
     """d lambda_1/d beta from the factor (L, D, X) of H at beta.
 
@@ -58,8 +71,9 @@ def analytic_grad(beta, mu_exact, L, D, X, k, n):
             c = mpm.mpf(0)
             for i in range(max(0, s_ - N + 1), min(s_, N - 1) + 1):
                 c += w[i] * w[s_ - i]
-            x = (s_ + 1) / b
-            mudot = -(mu_exact(s_) / b) * (1 + x * mpm.digamma(x))
+            xq = Fraction(s_ + 1) / Fraction(beta)   # (s+1)/beta, exact
+            x = mpm.mpf(xq.numerator) / xq.denominator
+            mudot = -(mu_exact(s_) / b) * (1 + x * psi(xq, mpm))
             total += mudot * c
         return total / (nu * nu), 1 / nu, nu
 

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 # every entry point declared in include/hk.h
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
            "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
-           "hk_div_batch"]
+           "hk_div_batch", "hk_set_profiling", "hk_get_profile"]
+PROFILE_FIELDS = 9
 
 
 class HKError(RuntimeError):
@@ -68,7 +69,9 @@ def load(path=LIB_PATH):
     L.hk_export.argtypes = [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _I32P, _I32P, _U32P]
     L.hk_fused_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 12 + [_P]
     L.hk_div_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 9 + [_P]
-    for name in ("hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
+    L.hk_set_profiling.argtypes = [_P, ctypes.c_int]
+    L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
+    for name in ("hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
                  "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -172,6 +175,19 @@ def hk_fused_batch(bits, count, a, x, y, out, stream=None):
 def hk_div_batch(bits, count, a, d, out, stream=None):
     args = [_P(p) for t in (a, d, out) for p in t]
     _check(load().hk_div_batch(bits, count, *args, _P(stream or 0)), what="hk_div_batch")
+
+
+def hk_set_profiling(ctx, on=True):
+    _check(load().hk_set_profiling(ctx, 1 if on else 0), ctx)
+
+
+def hk_get_profile(ctx):
+    """dict of the counters described in include/hk.h (hk_get_profile)."""
+    out = np.zeros(PROFILE_FIELDS, np.float64)
+    _check(load().hk_get_profile(ctx, _ptr(out, ctypes.c_double), PROFILE_FIELDS), ctx)
+    keys = ["launches", "trailing_ms", "trailing_launches", "trailing_limb_macs", "moments_ms", "ldlt_ms",
+            "invblock_ms", "eig_ms", "grad_ms"]
+    return dict(zip(keys, out.tolist()))
 
 
 # --- layout helpers (host-side marshalling) ---------------------------------

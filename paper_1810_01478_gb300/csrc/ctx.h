@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -38,6 +39,19 @@ struct Ctx {
   DevVec mu, A, U, X, S, evec, scratch;
   uint32_t* rec = nullptr;    // pivot reciprocal scratch (n limbs)
   int* rec_meta = nullptr;
+  // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
+  std::map<std::string, DevVec> pool;
+  void* d_tasks = nullptr;    // task descriptors of the current launch
+  size_t tasks_cap = 0;
+  // profiling (hk_set_profiling): CUDA events around every trailing-update
+  // launch and every stage, and a count of kernel launches
+  bool prof = false;
+  int64_t launches = 0;
+  std::vector<cudaEvent_t> events;
+  size_t ev_used = 0;
+  std::vector<std::pair<size_t, size_t>> trail_ev;
+  double trail_macs = 0.0;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> stage_ev;  // (stage id, events)
   // eigen results (host copies, filled by the lambda stage)
   int n_eig = 0;
   std::vector<int32_t> lam_sgn, lam_exp;
@@ -61,5 +75,15 @@ struct OpsTable {
 };
 
 const OpsTable* ops_for(int M);
+
+// next profiling event recorded on the context's stream (prof must be on)
+size_t prof_mark(Ctx& c);
+// count one kernel launch
+inline void count_launch(Ctx& c, int64_t k = 1) { c.launches += k; }
+
+// pool array `name` with at least `count` numbers of c.n limbs
+DevVec* pool_get(Ctx& c, const std::string& name, int64_t count);
+// device copy of a host byte range into the task buffer (stream ordered)
+hk_status upload_tasks(Ctx& c, const void* host, size_t bytes);
 
 }  // namespace hk

@@ -54,6 +54,47 @@ hk_status check_cuda(Ctx& c, cudaError_t e, const char* what) {
   return set_error(c, s, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+DevVec* pool_get(Ctx& c, const std::string& name, int64_t count) {
+  DevVec& v = c.pool[name];
+  if (v.count >= count && v.n == c.n && v.mant) return &v;
+  if (v.mant) cudaStreamSynchronize(c.stream);  // earlier kernels may still read it
+  dev_free(v);
+  if (dev_alloc(v, count, c.n) != cudaSuccess) {
+    set_error(c, HK_ERR_NOMEM, "allocating scratch " + name);
+    dev_free(v);
+    return nullptr;
+  }
+  return &v;
+}
+
+hk_status upload_tasks(Ctx& c, const void* host, size_t bytes) {
+  if (bytes > c.tasks_cap) {
+    if (c.d_tasks) {
+      cudaStreamSynchronize(c.stream);
+      cudaFree(c.d_tasks);
+      c.d_tasks = nullptr;
+    }
+    size_t cap = 1 << 16;
+    while (cap < bytes) cap <<= 1;
+    hk_status st = check_cuda(c, cudaMalloc(&c.d_tasks, cap), "allocating task buffer");
+    if (st != HK_OK) return st;
+    c.tasks_cap = cap;
+  }
+  // pageable source: the call returns once the bytes are staged, so the host
+  // vector may be released; the device copy is ordered before later kernels
+  return check_cuda(c, cudaMemcpyAsync(c.d_tasks, host, bytes, cudaMemcpyHostToDevice, c.stream), "task upload");
+}
+
+size_t prof_mark(Ctx& c) {
+  if (c.ev_used == c.events.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c.events.push_back(e);
+  }
+  cudaEventRecord(c.events[c.ev_used], c.stream);
+  return c.ev_used++;
+}
+
 hk_status read_device_flags(Ctx& c) {
   hk_status st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising");
   if (st != HK_OK) return st;
@@ -127,6 +168,9 @@ void hk_destroy(hk_ctx* h) {
   dev_free(c.S);
   dev_free(c.evec);
   dev_free(c.scratch);
+  for (auto& kv : c.pool) dev_free(kv.second);
+  if (c.d_tasks) cudaFree(c.d_tasks);
+  for (cudaEvent_t e : c.events) cudaEventDestroy(e);
   if (c.rec) cudaFree(c.rec);
   if (c.d_err) cudaFree(c.d_err);
   delete h;
@@ -172,7 +216,10 @@ hk_status hk_moments(hk_ctx* h, int64_t beta_num, int64_t beta_den, int N, int b
                                                (int)(cap * 4)),
                        "smem attribute")) != HK_OK)
     return st;
+  const size_t pe0 = c.prof ? prof_mark(c) : 0;
   k_moments_exact<<<1, 32, cap * 4, c.stream>>>((int)m, N, c.n, (int)cap, c.mu.view(), c.d_err);
+  count_launch(c);
+  if (c.prof) c.stage_ev.push_back({0, {pe0, prof_mark(c)}});
   if ((st = check_cuda(c, cudaGetLastError(), "launching the moments")) != HK_OK) return st;
   c.beta_num = beta_num;
   c.beta_den = beta_den;
@@ -206,7 +253,9 @@ hk_status hk_ldlt(hk_ctx* h) {
   if (st != HK_OK) return st;
   Ctx& c = h->c;
   if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_ldlt before the moments");
+  const size_t pe0 = c.prof ? prof_mark(c) : 0;
   st = ops_for(c.M)->ldlt(c);
+  if (c.prof) c.stage_ev.push_back({1, {pe0, prof_mark(c)}});
   if (st == HK_OK) c.stage = ST_LDLT;
   return st;
 }
@@ -218,7 +267,9 @@ hk_status hk_inv_block(hk_ctx* h, int k) {
   if (c.stage < ST_LDLT) return set_error(c, HK_ERR_ORDER, "hk_inv_block before hk_ldlt");
   if (k < 1 || k > c.N || k > 64) return set_error(c, HK_ERR_ARG, "k must be in 1..min(N, 64)");
   c.k = k;
+  const size_t pe0 = c.prof ? prof_mark(c) : 0;
   st = ops_for(c.M)->inv_block(c);
+  if (c.prof) c.stage_ev.push_back({2, {pe0, prof_mark(c)}});
   if (st == HK_OK) c.stage = ST_INVBLOCK;
   return st;
 }
@@ -230,7 +281,9 @@ hk_status hk_lambda1(hk_ctx* h, int n_eig, int32_t* sign, int32_t* exp, uint32_t
   Ctx& c = h->c;
   if (c.stage < ST_INVBLOCK) return set_error(c, HK_ERR_ORDER, "hk_lambda1 before hk_inv_block");
   if (n_eig < 1 || n_eig > 3 || n_eig > c.k) return set_error(c, HK_ERR_ARG, "n_eig must be in 1..min(3, k)");
+  const size_t pe0 = c.prof ? prof_mark(c) : 0;
   if ((st = ops_for(c.M)->lambda(c, n_eig)) != HK_OK) return st;
+  if (c.prof) c.stage_ev.push_back({3, {pe0, prof_mark(c)}});
   if ((st = read_device_flags(c)) != HK_OK) return st;
   for (int m = 0; m < n_eig; ++m) {
     if (sign) sign[m] = c.lam_sgn[m];
@@ -250,7 +303,9 @@ hk_status hk_lambda1_grad(hk_ctx* h, int32_t* sign, int32_t* exp, uint32_t* limb
   if (c.stage < ST_LAMBDA) return set_error(c, HK_ERR_ORDER, "hk_lambda1_grad before hk_lambda1");
   if (c.beta_den <= 0 || c.beta_num <= 0 || c.beta_den % c.beta_num != 0)
     return set_error(c, HK_ERR_UNSUPPORTED, "the gradient needs beta = 1/m");
+  const size_t pe0 = c.prof ? prof_mark(c) : 0;
   if ((st = ops_for(c.M)->grad(c, sign, exp, limbs, f64)) != HK_OK) return st;
+  if (c.prof) c.stage_ev.push_back({4, {pe0, prof_mark(c)}});
   return read_device_flags(c);
 }
 
@@ -292,6 +347,45 @@ hk_status hk_export(hk_ctx* h, int what, int64_t first, int64_t count, int32_t* 
     return HK_OK;
   }
   return count ? copy(0, base + first, count) : HK_OK;
+}
+
+hk_status hk_set_profiling(hk_ctx* h, int on) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if ((st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising")) != HK_OK) return st;
+  c.prof = on != 0;
+  c.ev_used = 0;
+  c.trail_ev.clear();
+  c.stage_ev.clear();
+  c.trail_macs = 0.0;
+  c.launches = 0;
+  return HK_OK;
+}
+
+hk_status hk_get_profile(hk_ctx* h, double* out, int cap) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (!out || cap < HK_PROFILE_FIELDS) return set_error(c, HK_ERR_ARG, "profile buffer too small");
+  if ((st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising")) != HK_OK) return st;
+  for (int i = 0; i < HK_PROFILE_FIELDS; ++i) out[i] = 0.0;
+  out[0] = (double)c.launches;
+  double tms = 0.0;
+  for (auto& p : c.trail_ev) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.events[p.first], c.events[p.second]);
+    tms += ms;
+  }
+  out[1] = tms;
+  out[2] = (double)c.trail_ev.size();
+  out[3] = c.trail_macs;
+  for (auto& p : c.stage_ev) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.events[p.second.first], c.events[p.second.second]);
+    out[4 + p.first] += ms;
+  }
+  return HK_OK;
 }
 
 static MPVec cvec(const int32_t* s, const int32_t* e, const uint32_t* m) {

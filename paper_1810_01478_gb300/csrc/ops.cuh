@@ -89,9 +89,11 @@ struct Ops {
       const int64_t work = tri * (n / 4);
       const int grid = (int)std::min<int64_t>((work + 255) / 256, 8 * sm_count(c.device) * 8);
       k_assemble<M><<<grid, 256, 0, s>>>(c.mu.view(), c.A.view(), N);
+      count_launch(c);
     }
     for (int i = 0; i < N; ++i) {
       k_recip_pivot<M><<<1, 32, recip_smem, s>>>(c.A.view(), N, i, c.rec, c.rec_meta, c.d_err);
+      count_launch(c);
       if (i == N - 1) break;
       const int64_t rows = N - 1 - i;
       const int gs = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, scale_res);
@@ -99,7 +101,13 @@ struct Ops {
       const int64_t m = rows;
       const int64_t T = m * (m + 1) / 2;
       const int gt = (int)std::min<int64_t>((T + WARPS - 1) / WARPS, trail_res);
+      const size_t e0 = c.prof ? prof_mark(c) : 0;
       k_trailing<M><<<gt, 32 * WARPS, fused_smem, s>>>(c.A.view(), c.U.view(), N, i, 0, T, c.d_err);
+      if (c.prof) {
+        c.trail_ev.push_back({e0, prof_mark(c)});
+        c.trail_macs += (double)T * n * n;  // n^2 limb products per fused operation
+      }
+      count_launch(c, 2);
     }
     return check_cuda(c, cudaGetLastError(), "launching the factorisation");
   }

@@ -1,15 +1,487 @@
-// Launchers of the stages after the factorisation (placeholders until the
-// kernels of those stages are in place).
+// Launchers of the stages after the factorisation:
+//   inv_block  Algorithm 4 (Sec. 4.4) and S = (H^{-1})[0:k,0:k] (Sec. 4.5)
+//   lambda     largest eigenvalues of S, lambda = 1/nu (Secs. 4.2, 4.5)
+//   grad       d lambda_1 / d beta (first-order perturbation of nu_1)
 #pragma once
+#include <cmath>
+#include <cstring>
+
+#include "euler_gamma.inc"
+#include "k_tail.cuh"
 #include "ops.cuh"
 
 namespace hk {
-template <int M>
-hk_status Ops<M>::inv_block(Ctx& c) { return set_error(c, HK_ERR_UNSUPPORTED, "inv_block not built"); }
-template <int M>
-hk_status Ops<M>::lambda(Ctx& c, int) { return set_error(c, HK_ERR_UNSUPPORTED, "lambda1 not built"); }
-template <int M>
-hk_status Ops<M>::grad(Ctx& c, int32_t*, int32_t*, uint32_t*, double*) {
-  return set_error(c, HK_ERR_UNSUPPORTED, "lambda1_grad not built");
+
+// a dot product sum_q x[x0 + q sx] * y[y0 + q sy] (q < len), negated if neg
+struct Dot {
+  int64_t out, x0, y0;
+  int32_t sx, sy, len;
+  bool neg;
+};
+
+static double to_double(int32_t s, int32_t e, const uint32_t* m, int n) {
+  if (m[n - 1] == 0) return 0.0;
+  // the top limb may hold a single bit: three limbs give >= 65 significant bits
+  const double v = ((double)m[n - 1] * 4294967296.0 + (double)m[n - 2]) * 4294967296.0 + (double)m[n - 3];
+  const double r = std::ldexp(v, 32 * (e + n - 3));
+  return s ? -r : r;
 }
+
+template <int M>
+struct Tail {
+  static constexpr int n = 32 * M;
+  static constexpr int W = Ops<M>::WARPS;
+  static constexpr int SEG = 16;  // chain length of one partial sum
+
+  static hk_status chains(Ctx& c, const std::vector<ChainTask>& t, MPVec X, MPVec Y, MPVec INIT, MPVec OUT) {
+    if (t.empty()) return HK_OK;
+    hk_status st = upload_tasks(c, t.data(), t.size() * sizeof(ChainTask));
+    if (st != HK_OK) return st;
+    const size_t smem = Ops<M>::fused_smem;
+    if ((st = check_cuda(c, allow_smem(k_chain<M>, smem), "smem attribute")) != HK_OK) return st;
+    const int res = Ops<M>::resident_blocks(k_chain<M>, 32 * W, smem, c.device);
+    const int grid = (int)std::min<int64_t>(((int64_t)t.size() + W - 1) / W, res);
+    k_chain<M><<<grid, 32 * W, smem, c.stream>>>(static_cast<const ChainTask*>(c.d_tasks), (int)t.size(), X, Y,
+                                                   INIT, OUT);
+    count_launch(c);
+    return check_cuda(c, cudaGetLastError(), "k_chain");
+  }
+
+  static hk_status quots(Ctx& c, const std::vector<QuotTask>& t, MPVec A, MPVec D, const DevVec& R, MPVec OUT) {
+    if (t.empty()) return HK_OK;
+    hk_status st = upload_tasks(c, t.data(), t.size() * sizeof(QuotTask));
+    if (st != HK_OK) return st;
+    const size_t smem = Ops<M>::div_smem;
+    if ((st = check_cuda(c, allow_smem(k_quot<M>, smem), "smem attribute")) != HK_OK) return st;
+    const int res = Ops<M>::resident_blocks(k_quot<M>, 32 * W, smem, c.device);
+    const int grid = (int)std::min<int64_t>(((int64_t)t.size() + W - 1) / W, res);
+    k_quot<M><<<grid, 32 * W, smem, c.stream>>>(static_cast<const QuotTask*>(c.d_tasks), (int)t.size(), A, D,
+                                                  R.mant, R.sgn, OUT, c.d_err);
+    count_launch(c);
+    return check_cuda(c, cudaGetLastError(), "k_quot");
+  }
+
+  // reciprocals of D[idx[i]] into slots [0, idx.size()) of R (mant = table, sgn = shifts)
+  static hk_status recips(Ctx& c, MPVec D, const std::vector<int64_t>& idx, const DevVec& R) {
+    if (idx.empty()) return HK_OK;
+    hk_status st = upload_tasks(c, idx.data(), idx.size() * sizeof(int64_t));
+    if (st != HK_OK) return st;
+    const size_t smem = (size_t)W * (3 * n + 4) * 4;
+    if ((st = check_cuda(c, allow_smem(k_recip_tab<M>, smem), "smem attribute")) != HK_OK) return st;
+    const int res = Ops<M>::resident_blocks(k_recip_tab<M>, 32 * W, smem, c.device);
+    const int grid = (int)std::min<int64_t>(((int64_t)idx.size() + W - 1) / W, res);
+    k_recip_tab<M><<<grid, 32 * W, smem, c.stream>>>(D, static_cast<const int64_t*>(c.d_tasks), 0, (int)idx.size(),
+                                                       R.mant, R.sgn, c.d_err);
+    count_launch(c);
+    return check_cuda(c, cudaGetLastError(), "k_recip_tab");
+  }
+
+  // out[i] = trunc(num[i] / den[i]) for small integers
+  static hk_status small(Ctx& c, const std::vector<int64_t>& num, const std::vector<int64_t>& den, MPVec OUT) {
+    if (num.empty()) return HK_OK;
+    std::vector<int64_t> both(num);
+    both.insert(both.end(), den.begin(), den.end());
+    hk_status st = upload_tasks(c, both.data(), both.size() * sizeof(int64_t));
+    if (st != HK_OK) return st;
+    const int cnt = (int)num.size();
+    const int64_t* d = static_cast<const int64_t*>(c.d_tasks);
+    k_small_ratio<M><<<(cnt + 127) / 128, 128, 0, c.stream>>>(d, d + cnt, cnt, OUT);
+    count_launch(c);
+    return check_cuda(c, cudaGetLastError(), "k_small_ratio");
+  }
+
+  // the constant 1 (pool "one")
+  static DevVec* one(Ctx& c) {
+    DevVec* v = pool_get(c, "one", 1);
+    if (v && small(c, {1}, {1}, v->view()) != HK_OK) return nullptr;
+    return v;
+  }
+
+  // dot products, split into chains of SEG terms whose partial sums are added
+  // by a second level of chains (recursively).
+  static hk_status dots(Ctx& c, const std::vector<Dot>& d, MPVec X, MPVec Y, MPVec OUT, int level = 0) {
+    if (d.empty()) return HK_OK;
+    int maxlen = 0;
+    for (const Dot& e : d) maxlen = std::max(maxlen, e.len);
+    if (maxlen <= 2 * SEG) {
+      std::vector<ChainTask> t;
+      t.reserve(d.size());
+      for (const Dot& e : d)
+        t.push_back(ChainTask{e.out, 0, e.x0, e.y0, e.sx, e.sy, e.len,
+                              CH_ZERO_INIT | CH_ADD | (e.neg ? CH_NEG_OUT : 0)});
+      return chains(c, t, X, Y, X, OUT);
+    }
+    int64_t total = 0;
+    for (const Dot& e : d) total += (e.len + SEG - 1) / SEG;
+    DevVec* P = pool_get(c, "partial" + std::to_string(level), total);
+    DevVec* ONE = one(c);
+    if (!P || !ONE) return c.sticky;
+    std::vector<ChainTask> t;
+    std::vector<Dot> up;
+    t.reserve(total);
+    int64_t base = 0;
+    for (const Dot& e : d) {
+      const int segs = (e.len + SEG - 1) / SEG;
+      for (int g = 0; g < segs; ++g) {
+        const int q0 = g * SEG, len = std::min(SEG, e.len - q0);
+        t.push_back(ChainTask{base + g, 0, e.x0 + (int64_t)q0 * e.sx, e.y0 + (int64_t)q0 * e.sy, e.sx, e.sy, len,
+                              CH_ZERO_INIT | CH_ADD});
+      }
+      up.push_back(Dot{e.out, 0, base, 0, 1, segs, e.neg});
+      base += segs;
+    }
+    hk_status st = chains(c, t, X, Y, X, P->view());
+    if (st != HK_OK) return st;
+    return dots(c, up, ONE->view(), P->view(), OUT, level + 1);
+  }
+
+  // ------------------------------------------------------------------------
+  // a5, a6
+  // ------------------------------------------------------------------------
+  static hk_status inv_block(Ctx& c) {
+    const int N = c.N, k = c.k;
+    hk_status st;
+    if (c.X.count != (int64_t)N * k || c.X.n != n) {
+      dev_free(c.X);
+      if ((st = check_cuda(c, dev_alloc(c.X, (int64_t)N * k, n), "allocating X")) != HK_OK) return st;
+    }
+    if (c.S.count != (int64_t)k * k || c.S.n != n) {
+      dev_free(c.S);
+      if ((st = check_cuda(c, dev_alloc(c.S, (int64_t)k * k, n), "allocating S")) != HK_OK) return st;
+    }
+    {
+      const int64_t work = (int64_t)N * k * n;
+      const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
+      k_x_init<M><<<grid, 256, 0, c.stream>>>(c.X.view(), N, k);
+      count_launch(c);
+    }
+    const size_t smem = Ops<M>::fused_smem;
+    if ((st = check_cuda(c, allow_smem(k_alg4_step<M>, smem), "smem attribute")) != HK_OK) return st;
+    const int res = Ops<M>::resident_blocks(k_alg4_step<M>, 32 * W, smem, c.device);
+    // Algorithm 4: N-1 steps in increasing pivot order
+    for (int i = 0; i < N - 1; ++i) {
+      const int64_t per_row = std::min(k, i) + (i < k ? 1 : 0);
+      const int64_t total = (int64_t)(N - 1 - i) * per_row;
+      if (total == 0) continue;
+      const int grid = (int)std::min<int64_t>((total + W - 1) / W, res);
+      k_alg4_step<M><<<grid, 32 * W, smem, c.stream>>>(c.A.view(), c.X.view(), N, k, i);
+      count_launch(c);
+    }
+    if ((st = check_cuda(c, cudaGetLastError(), "Algorithm 4")) != HK_OK) return st;
+    // reciprocals of the pivots (kept for the gradient), then Y[l][b] = X[l][b] / D_l
+    DevVec* Rd = pool_get(c, "recip_d", N);
+    DevVec* Yq = pool_get(c, "xq", (int64_t)N * k);
+    if (!Rd || !Yq) return c.sticky;
+    std::vector<int64_t> diag(N);
+    for (int l = 0; l < N; ++l) diag[l] = tri_pos(N, l, l);
+    if ((st = recips(c, c.A.view(), diag, *Rd)) != HK_OK) return st;
+    std::vector<QuotTask> qt;
+    for (int l = 0; l < N; ++l)
+      for (int b = 0; b <= std::min(l, k - 1); ++b)
+        qt.push_back(QuotTask{(int64_t)l * k + b, (int64_t)l * k + b, diag[l], l, 0, 0});
+    if ((st = quots(c, qt, c.X.view(), c.A.view(), *Rd, Yq->view())) != HK_OK) return st;
+    // S_ab = sum_{l >= b} X[l][a] * Y[l][b]  (a <= b), then the mirror image
+    std::vector<Dot> dd;
+    for (int a = 0; a < k; ++a)
+      for (int b = a; b < k; ++b)
+        dd.push_back(Dot{(int64_t)a * k + b, (int64_t)b * k + a, (int64_t)b * k + b, k, k, N - b, false});
+    if ((st = dots(c, dd, c.X.view(), Yq->view(), c.S.view())) != HK_OK) return st;
+    std::vector<ChainTask> mirror;
+    for (int a = 0; a < k; ++a)
+      for (int b = a + 1; b < k; ++b)
+        mirror.push_back(ChainTask{(int64_t)b * k + a, (int64_t)a * k + b, 0, 0, 0, 0, 0, 0});
+    return chains(c, mirror, c.S.view(), c.S.view(), c.S.view(), c.S.view());
+  }
+
+  // ------------------------------------------------------------------------
+  // a7: largest eigenvalue of the leading kk x kk block of the k x k matrix Sm
+  // ------------------------------------------------------------------------
+  // T = Sm^(2^s) by repeated squaring (T -> nu_1^(2^s) u u^T), v = the column
+  // of T with the largest diagonal entry, nu = v^T Sm v / v^T v (Rayleigh
+  // quotient, error ~ (nu_2/nu_1)^(2^(s+1))).  Writes v (kk numbers) into V
+  // and nu, v^T v into scal[slot], scal[slot + 1].
+  static hk_status eig_top(Ctx& c, MPVec Sm, int k, int kk, int s, MPVec V, DevVec& scal, int slot) {
+    DevVec* T0 = pool_get(c, "T0", (int64_t)k * k);
+    DevVec* T1 = pool_get(c, "T1", (int64_t)k * k);
+    DevVec* Wv = pool_get(c, "w", k);
+    DevVec* Rs = pool_get(c, "recip_s", 4);
+    if (!T0 || !T1 || !Wv || !Rs) return c.sticky;
+    hk_status st;
+    std::vector<ChainTask> cp;
+    for (int a = 0; a < kk; ++a)
+      for (int b = 0; b < kk; ++b)
+        cp.push_back(ChainTask{(int64_t)a * k + b, (int64_t)a * k + b, 0, 0, 0, 0, 0, 0});
+    if ((st = chains(c, cp, Sm, Sm, Sm, T0->view())) != HK_OK) return st;
+    for (int it = 0; it < s; ++it) {
+      std::vector<Dot> sq;
+      for (int a = 0; a < kk; ++a)
+        for (int b = 0; b < kk; ++b)
+          sq.push_back(Dot{(int64_t)a * k + b, (int64_t)a * k, b, 1, k, kk, false});
+      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view())) != HK_OK) return st;
+      std::swap(*T0, *T1);
+    }
+    int* d_j = c.d_err + 4;
+    k_argmax_diag<<<1, 32, 0, c.stream>>>(T0->view(), k, kk, n, d_j);
+    count_launch(c);
+    int j = 0;
+    if ((st = check_cuda(c, cudaMemcpyAsync(&j, d_j, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "argmax")) ||
+        (st = check_cuda(c, cudaStreamSynchronize(c.stream), "argmax sync")))
+      return st;
+    std::vector<ChainTask> col;
+    for (int a = 0; a < kk; ++a) col.push_back(ChainTask{a, (int64_t)a * k + j, 0, 0, 0, 0, 0, 0});
+    if ((st = chains(c, col, T0->view(), T0->view(), T0->view(), V)) != HK_OK) return st;
+    std::vector<Dot> sv;
+    for (int a = 0; a < kk; ++a) sv.push_back(Dot{a, (int64_t)a * k, 0, 1, 1, kk, false});
+    if ((st = dots(c, sv, Sm, V, Wv->view())) != HK_OK) return st;
+    DevVec* tmp = pool_get(c, "eig_tmp", 2);
+    if (!tmp) return c.sticky;
+    if ((st = dots(c, {Dot{0, 0, 0, 1, 1, kk, false}}, V, Wv->view(), tmp->view())) != HK_OK) return st;
+    if ((st = dots(c, {Dot{1, 0, 0, 1, 1, kk, false}}, V, V, tmp->view())) != HK_OK) return st;
+    if ((st = recips(c, tmp->view(), {1}, *Rs)) != HK_OK) return st;
+    // nu = num / den;  copy den
+    if ((st = quots(c, {QuotTask{slot, 0, 1, 0, 0, 0}}, tmp->view(), tmp->view(), *Rs, scal.view())) != HK_OK)
+      return st;
+    return chains(c, {ChainTask{slot + 1, 1, 0, 0, 0, 0, 0, 0}}, tmp->view(), tmp->view(), tmp->view(), scal.view());
+  }
+
+  // Sm <- Sm - (nu / v^T v) v v^T on the leading kk block (removes nu from the spectrum)
+  static hk_status deflate(Ctx& c, MPVec Sm, int k, int kk, MPVec V, DevVec& scal, int slot) {
+    DevVec* Rs = pool_get(c, "recip_s", 4);
+    DevVec* cv = pool_get(c, "cv", k);
+    DevVec* cf = pool_get(c, "cf", 1);
+    if (!Rs || !cv || !cf) return c.sticky;
+    hk_status st;
+    if ((st = recips(c, scal.view(), {(int64_t)slot + 1}, *Rs)) != HK_OK) return st;
+    if ((st = quots(c, {QuotTask{0, slot, slot + 1, 0, 0, 0}}, scal.view(), scal.view(), *Rs, cf->view())) != HK_OK)
+      return st;
+    std::vector<Dot> cvd;
+    for (int a = 0; a < kk; ++a) cvd.push_back(Dot{a, 0, a, 0, 0, 1, false});
+    if ((st = dots(c, cvd, cf->view(), V, cv->view())) != HK_OK) return st;
+    std::vector<ChainTask> t;
+    for (int a = 0; a < kk; ++a)
+      for (int b = 0; b < kk; ++b)
+        t.push_back(ChainTask{(int64_t)a * k + b, (int64_t)a * k + b, a, b, 0, 0, 1, 0});
+    return chains(c, t, cv->view(), V, Sm, Sm);
+  }
+
+  static int squarings_for(int bits_target) {
+    // (nu_2/nu_1)^(2^(s+1)) < 2^-bits_target when nu_2/nu_1 <= 1/2
+    int s = 1;
+    while ((1 << (s + 1)) < bits_target) ++s;
+    return s + 2;
+  }
+
+  // eigenvalues of the leading kk block: lam[m] = 1/nu_m (m < ne) into LAM[m]
+  static hk_status block_lambdas(Ctx& c, int kk, int ne, int s, MPVec LAM, bool keep_vector) {
+    const int k = c.k;
+    DevVec* Sw = pool_get(c, "Sw", (int64_t)k * k);
+    DevVec* V = pool_get(c, "v", k);
+    DevVec* scal = pool_get(c, "scal", 16);
+    DevVec* Rs = pool_get(c, "recip_s", 4);
+    DevVec* ONE = one(c);
+    if (!Sw || !V || !scal || !Rs || !ONE) return c.sticky;
+    hk_status st;
+    std::vector<ChainTask> cp;
+    for (int64_t e = 0; e < (int64_t)k * k; ++e) cp.push_back(ChainTask{e, e, 0, 0, 0, 0, 0, 0});
+    if ((st = chains(c, cp, c.S.view(), c.S.view(), c.S.view(), Sw->view())) != HK_OK) return st;
+    for (int m = 0; m < ne; ++m) {
+      if ((st = eig_top(c, Sw->view(), k, kk, s, V->view(), *scal, 2 * m)) != HK_OK) return st;
+      if (m == 0 && keep_vector) {
+        DevVec* E1 = pool_get(c, "eig1", 2);  // nu_1, v^T v
+        if (!E1) return c.sticky;
+        if (c.evec.count != k || c.evec.n != n) {
+          dev_free(c.evec);
+          if ((st = check_cuda(c, dev_alloc(c.evec, k, n), "allocating evec")) != HK_OK) return st;
+        }
+        std::vector<ChainTask> cv;
+        for (int a = 0; a < k; ++a) cv.push_back(ChainTask{a, a, 0, 0, 0, 0, 0, a < kk ? 0 : CH_ZERO_INIT});
+        if ((st = chains(c, cv, V->view(), V->view(), V->view(), c.evec.view())) != HK_OK) return st;
+        if ((st = chains(c, {ChainTask{0, 0, 0, 0, 0, 0, 0, 0}, ChainTask{1, 1, 0, 0, 0, 0, 0, 0}}, scal->view(),
+                         scal->view(), scal->view(), E1->view())) != HK_OK)
+          return st;
+      }
+      if (m + 1 < ne && (st = deflate(c, Sw->view(), k, kk, V->view(), *scal, 2 * m)) != HK_OK) return st;
+    }
+    // lambda_m = 1 / nu_m
+    std::vector<int64_t> nus;
+    for (int m = 0; m < ne; ++m) nus.push_back(2 * m);
+    if ((st = recips(c, scal->view(), nus, *Rs)) != HK_OK) return st;
+    std::vector<QuotTask> q;
+    for (int m = 0; m < ne; ++m) q.push_back(QuotTask{m, 0, 2 * m, m, 0, 0});
+    return quots(c, q, ONE->view(), scal->view(), *Rs, LAM);
+  }
+
+  static hk_status lambda(Ctx& c, int n_eig) {
+    const int k = c.k;
+    hk_status st;
+    DevVec* LAM = pool_get(c, "lam", 3);
+    DevVec* LAM1 = pool_get(c, "lam_km1", 3);
+    DevVec* DIF = pool_get(c, "lam_diff", 3);
+    if (!LAM || !LAM1 || !DIF) return c.sticky;
+    if ((st = block_lambdas(c, k, n_eig, squarings_for(32 * n + 64), LAM->view(), true)) != HK_OK) return st;
+    const int ne1 = std::min(n_eig, k - 1);
+    if (ne1 > 0) {
+      // the (k-1) x (k-1) estimate only feeds a double-precision difference
+      if ((st = block_lambdas(c, k - 1, ne1, squarings_for(640), LAM1->view(), false)) != HK_OK) return st;
+      DevVec* ONE = one(c);
+      if (!ONE) return c.sticky;
+      std::vector<ChainTask> t;
+      for (int m = 0; m < ne1; ++m) t.push_back(ChainTask{m, m, 0, m, 0, 0, 1, 0});
+      // lam(k) - 1 * lam(k-1)
+      if ((st = chains(c, t, ONE->view(), LAM1->view(), LAM->view(), DIF->view())) != HK_OK) return st;
+    }
+    if ((st = read_device_flags(c)) != HK_OK) return st;
+    c.n_eig = n_eig;
+    c.lam_sgn.assign(n_eig, 0);
+    c.lam_exp.assign(n_eig, 0);
+    c.lam_mant.assign((size_t)n_eig * n, 0);
+    c.lam_f64.assign(n_eig, 0.0);
+    c.trunc_f64.assign(n_eig, NAN);
+    std::vector<int32_t> ds(3), de(3);
+    std::vector<uint32_t> dm(3 * n);
+    if ((st = check_cuda(c, cudaMemcpy(c.lam_sgn.data(), LAM->sgn, n_eig * 4, cudaMemcpyDeviceToHost), "D2H")) ||
+        (st = check_cuda(c, cudaMemcpy(c.lam_exp.data(), LAM->exp, n_eig * 4, cudaMemcpyDeviceToHost), "D2H")) ||
+        (st = check_cuda(c, cudaMemcpy(c.lam_mant.data(), LAM->mant, (size_t)n_eig * n * 4, cudaMemcpyDeviceToHost),
+                         "D2H")))
+      return st;
+    for (int m = 0; m < n_eig; ++m)
+      c.lam_f64[m] = to_double(c.lam_sgn[m], c.lam_exp[m], c.lam_mant.data() + (size_t)m * n, n);
+    if (ne1 > 0) {
+      if ((st = check_cuda(c, cudaMemcpy(ds.data(), DIF->sgn, ne1 * 4, cudaMemcpyDeviceToHost), "D2H")) ||
+          (st = check_cuda(c, cudaMemcpy(de.data(), DIF->exp, ne1 * 4, cudaMemcpyDeviceToHost), "D2H")) ||
+          (st = check_cuda(c, cudaMemcpy(dm.data(), DIF->mant, (size_t)ne1 * n * 4, cudaMemcpyDeviceToHost), "D2H")))
+        return st;
+      for (int m = 0; m < ne1; ++m) c.trunc_f64[m] = to_double(ds[m], de[m], dm.data() + (size_t)m * n, n);
+    }
+    return HK_OK;
+  }
+
+  // ------------------------------------------------------------------------
+  // a8: d lambda_1 / d beta = (w^T Hdot w) / (nu_1^2 v^T v),
+  //     w = L^{-T} D^{-1} X v,  Hdot_ij = mudot_{i+j},
+  //     mudot_s = -m mu_s (1 + m(s+1) (H_{m(s+1)-1} - gamma))   for beta = 1/m
+  // ------------------------------------------------------------------------
+  static hk_status grad(Ctx& c, int32_t* osgn, int32_t* oexp, uint32_t* omant, double* of64) {
+    const int N = c.N, k = c.k;
+    const int64_t m = c.beta_den / c.beta_num;
+    hk_status st;
+    DevVec* Rd = pool_get(c, "recip_d", N);
+    DevVec* E1 = pool_get(c, "eig1", 2);
+    DevVec* z = pool_get(c, "gz", 2 * N - 1);  // z = X v (N), later q_s and mudot_s (2N-1)
+    DevVec* y = pool_get(c, "gy", N);
+    DevVec* cs = pool_get(c, "gc", 2 * N - 1);
+    const int64_t tmax = m * (2 * N - 1) - 1;
+    DevVec* H0 = pool_get(c, "gh0", tmax + 1);
+    DevVec* H1 = pool_get(c, "gh1", tmax + 1);
+    DevVec* hq = pool_get(c, "ghq", 2 * N - 1);
+    DevVec* kint = pool_get(c, "gk", 2 * N - 1);
+    DevVec* cst = pool_get(c, "gconst", 4);  // 0: m, 1: gamma
+    DevVec* res = pool_get(c, "gres", 4);
+    DevVec* Rs = pool_get(c, "recip_s", 4);
+    DevVec* ONE = one(c);
+    if (!Rd || !E1 || !z || !y || !cs || !H0 || !H1 || !hq || !kint || !cst || !res || !Rs || !ONE) return c.sticky;
+    // z = X v, y = D^{-1} z
+    std::vector<Dot> zd;
+    for (int l = 0; l < N; ++l) zd.push_back(Dot{l, (int64_t)l * k, 0, 1, 1, std::min(l + 1, k), false});
+    if ((st = dots(c, zd, c.X.view(), c.evec.view(), z->view())) != HK_OK) return st;
+    std::vector<QuotTask> qt;
+    for (int l = 0; l < N; ++l) qt.push_back(QuotTask{l, l, tri_pos(N, l, l), l, 0, 0});
+    if ((st = quots(c, qt, z->view(), c.A.view(), *Rd, y->view())) != HK_OK) return st;
+    // w = L^{-T} y by column back substitution
+    {
+      const size_t smem = Ops<M>::fused_smem;
+      if ((st = check_cuda(c, allow_smem(k_backsub_step<M>, smem), "smem attribute")) != HK_OK) return st;
+      const int resb = Ops<M>::resident_blocks(k_backsub_step<M>, 32 * W, smem, c.device);
+      for (int j = N - 1; j >= 1; --j) {
+        const int grid = std::min((j + W - 1) / W, resb);
+        k_backsub_step<M><<<grid, 32 * W, smem, c.stream>>>(c.A.view(), y->view(), N, j);
+        count_launch(c);
+      }
+      if ((st = check_cuda(c, cudaGetLastError(), "back substitution")) != HK_OK) return st;
+    }
+    // c_s = sum_{i+j=s} w_i w_j
+    std::vector<Dot> cd;
+    for (int s = 0; s <= 2 * N - 2; ++s) {
+      const int lo = std::max(0, s - N + 1), hi = std::min(s, N - 1);
+      cd.push_back(Dot{s, lo, s - lo, 1, -1, hi - lo + 1, false});
+    }
+    if ((st = dots(c, cd, y->view(), y->view(), cs->view())) != HK_OK) return st;
+    // harmonic numbers H_t = sum_{j<=t} 1/j (Hillis-Steele scan of the reciprocals)
+    {
+      std::vector<int64_t> num(tmax + 1, 1), den(tmax + 1);
+      num[0] = 0;
+      for (int64_t j = 0; j <= tmax; ++j) den[j] = j ? j : 1;
+      if ((st = small(c, num, den, H0->view())) != HK_OK) return st;
+      for (int64_t d = 1; d <= tmax; d <<= 1) {
+        std::vector<ChainTask> t;
+        t.reserve(tmax + 1);
+        for (int64_t i = 0; i <= tmax; ++i)
+          t.push_back(i >= d ? ChainTask{i, i, 0, i - d, 0, 0, 1, CH_ADD} : ChainTask{i, i, 0, 0, 0, 0, 0, 0});
+        if ((st = chains(c, t, ONE->view(), H0->view(), H0->view(), H1->view())) != HK_OK) return st;
+        std::swap(*H0, *H1);
+      }
+    }
+    // constants m and gamma
+    if ((st = small(c, {m}, {1}, cst->view())) != HK_OK) return st;
+    {
+      std::vector<uint32_t> g(n);
+      for (int i = 0; i < n; ++i) g[i] = hk_euler_gamma[HK_GAMMA_LIMBS - n + i];
+      const int32_t gs = 0, ge = -n;
+      if ((st = check_cuda(c, cudaMemcpyAsync(cst->sgn + 1, &gs, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+          (st = check_cuda(c, cudaMemcpyAsync(cst->exp + 1, &ge, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+          (st = check_cuda(c, cudaMemcpyAsync(cst->mant + n, g.data(), (size_t)n * 4, cudaMemcpyHostToDevice,
+                                              c.stream), "H2D")) ||
+          (st = check_cuda(c, cudaStreamSynchronize(c.stream), "H2D sync")))
+        return st;
+    }
+    // h_s = H_{m(s+1)-1} - gamma ; q_s = 1 + m(s+1) h_s ; p_s = mu_s q_s ; mudot_s = -m p_s
+    std::vector<int64_t> kn, kd;
+    for (int s = 0; s <= 2 * N - 2; ++s) { kn.push_back(m * (s + 1)); kd.push_back(1); }
+    if ((st = small(c, kn, kd, kint->view())) != HK_OK) return st;
+    std::vector<ChainTask> t1, t2, t3, t4;
+    for (int s = 0; s <= 2 * N - 2; ++s) {
+      t1.push_back(ChainTask{s, m * (s + 1) - 1, 0, 1, 0, 0, 1, 0});             // H - 1*gamma
+      t2.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ADD});                      // 1 + kint*h
+      t3.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ZERO_INIT | CH_ADD});       // mu*q
+      t4.push_back(ChainTask{s, 0, 0, s, 0, 0, 1, CH_ZERO_INIT});                // -m*p
+    }
+    if ((st = chains(c, t1, ONE->view(), cst->view(), H0->view(), hq->view())) != HK_OK) return st;
+    if ((st = chains(c, t2, kint->view(), hq->view(), ONE->view(), z->view())) != HK_OK) return st;
+    if ((st = chains(c, t3, c.mu.view(), z->view(), z->view(), hq->view())) != HK_OK) return st;
+    if ((st = chains(c, t4, cst->view(), hq->view(), hq->view(), z->view())) != HK_OK) return st;
+    // g = sum_s mudot_s c_s ; t = nu^2 (v^T v) ; result = g / t
+    if ((st = dots(c, {Dot{0, 0, 0, 1, 1, 2 * N - 1, false}}, z->view(), cs->view(), res->view())) != HK_OK)
+      return st;
+    if ((st = chains(c, {ChainTask{1, 0, 0, 0, 0, 0, 1, CH_ZERO_INIT | CH_ADD}}, E1->view(), E1->view(), E1->view(),
+                     res->view())) != HK_OK)
+      return st;
+    if ((st = chains(c, {ChainTask{2, 0, 1, 1, 0, 0, 1, CH_ZERO_INIT | CH_ADD}}, res->view(), E1->view(),
+                     res->view(), res->view())) != HK_OK)
+      return st;
+    if ((st = recips(c, res->view(), {2}, *Rs)) != HK_OK) return st;
+    if ((st = quots(c, {QuotTask{3, 0, 2, 0, 0, 0}}, res->view(), res->view(), *Rs, res->view())) != HK_OK)
+      return st;
+    if ((st = read_device_flags(c)) != HK_OK) return st;
+    int32_t s_ = 0, e_ = 0;
+    std::vector<uint32_t> mm(n);
+    if ((st = check_cuda(c, cudaMemcpy(&s_, res->sgn + 3, 4, cudaMemcpyDeviceToHost), "D2H")) ||
+        (st = check_cuda(c, cudaMemcpy(&e_, res->exp + 3, 4, cudaMemcpyDeviceToHost), "D2H")) ||
+        (st = check_cuda(c, cudaMemcpy(mm.data(), res->mant + 3 * (int64_t)n, (size_t)n * 4, cudaMemcpyDeviceToHost),
+                         "D2H")))
+      return st;
+    if (osgn) *osgn = s_;
+    if (oexp) *oexp = e_;
+    if (omant) std::memcpy(omant, mm.data(), (size_t)n * 4);
+    if (of64) *of64 = to_double(s_, e_, mm.data(), n);
+    return HK_OK;
+  }
+};
+
+template <int M>
+hk_status Ops<M>::inv_block(Ctx& c) { return Tail<M>::inv_block(c); }
+template <int M>
+hk_status Ops<M>::lambda(Ctx& c, int n_eig) { return Tail<M>::lambda(c, n_eig); }
+template <int M>
+hk_status Ops<M>::grad(Ctx& c, int32_t* s, int32_t* e, uint32_t* m, double* f) { return Tail<M>::grad(c, s, e, m, f); }
+
 }  // namespace hk

@@ -1,0 +1,95 @@
+"""Writes the oracle's expected values for workloads too slow to run inside a test.
+
+Calls only ``oracle/``.  Each target runs the oracle pipeline (moments ->
+Algorithm 1 -> Algorithm 4 -> block -> eigenvalues, and the gradient where
+asked) and stores, in tests/golden/<name>.json:
+  lambdas / trunc_errors  as decimal strings (80 significant digits)
+  grad, grad_fd           analytic d lambda_1/d beta and the central
+                          difference at beta +- 1e-30 (where asked)
+  factor_sha256           SHA-256 of the packed factor in the library's export
+                          order: for c in 0..N-1, r in c..N-1 the entry
+                          (D_c on the diagonal, L[r][c] below) as int32 sign,
+                          int32 exp, n uint32 limbs, all little endian
+  x_sha256                the same for X (row major N x k)
+Usage:  python tests/golden/make_golden.py <target> [<target> ...]
+Targets: c1, c2, c5_512_4096, c5_768_4096, c5_1024_4096, c5_1024_8192
+"""
+import hashlib
+import json
+import os
+import struct
+import sys
+import time
+from fractions import Fraction
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import mpfloat as F       # noqa: E402
+from oracle import pipeline as PL     # noqa: E402
+from oracle import grad as GR         # noqa: E402
+
+TARGETS = {
+    "c1": dict(beta=(1, 2), N=48, k=8, bits=4096, grad=True, fd=False),
+    "c2": dict(beta=(1, 2), N=256, k=16, bits=8192, grad=True, fd=True),
+    "c5_512_4096": dict(beta=(1, 2), N=512, k=32, bits=4096, grad=False, fd=False),
+    "c5_768_4096": dict(beta=(1, 2), N=768, k=32, bits=4096, grad=False, fd=False),
+    "c5_1024_4096": dict(beta=(1, 2), N=1024, k=32, bits=4096, grad=False, fd=False),
+    "c5_1024_8192": dict(beta=(1, 2), N=1024, k=32, bits=8192, grad=False, fd=False),
+}
+
+
+def num_bytes(x, n):
+    s, e, limbs = F.limbs_of(x, n)
+    return struct.pack("<ii", s, e) + struct.pack("<%dI" % n, *limbs)
+
+
+def factor_digest(D, L, N, n):
+    h = hashlib.sha256()
+    for c in range(N):
+        for r in range(c, N):
+            h.update(num_bytes(D[c] if r == c else L[r][c], n))
+    return h.hexdigest()
+
+
+def x_digest(X, N, k, n):
+    h = hashlib.sha256()
+    for r in range(N):
+        for c in range(k):
+            h.update(num_bytes(X[r][c], n))
+    return h.hexdigest()
+
+
+def run(name):
+    import mpmath as mpm
+    cfg = TARGETS[name]
+    N, k, bits = cfg["N"], cfg["k"], cfg["bits"]
+    n = bits // 32
+    beta = Fraction(*cfg["beta"])
+    t0 = time.time()
+    r = PL.run(beta, N, k, n)
+    out = dict(name=name, beta=list(cfg["beta"]), N=N, k=k, bits=bits,
+               source="tests/golden/make_golden.py (oracle only)")
+    with mpm.workprec(r["prec"]):
+        out["lambdas"] = [mpm.nstr(v, 80) for v in r["lambdas"]]
+        out["trunc_errors"] = [mpm.nstr(v, 30) for v in r["trunc_errors"]]
+    out["factor_sha256"] = factor_digest(r["D"], r["L"], N, n)
+    out["x_sha256"] = x_digest(r["X"], N, r["k"], n)
+    if cfg["grad"]:
+        m = beta.denominator // beta.numerator
+        with mpm.workprec(2 * bits + 64):
+            g, _, _ = GR.analytic_grad(beta, lambda s: m * mpm.factorial(m * (s + 1) - 1), r["L"], r["D"], r["X"],
+                                       r["k"], n)
+            out["grad"] = mpm.nstr(g, 80)
+    if cfg["fd"]:
+        with mpm.workprec(2 * bits + 64):
+            out["grad_fd"] = mpm.nstr(GR.fd_grad(beta, N, k, n, h_exp=-30), 80)
+    out["oracle_seconds"] = round(time.time() - t0, 1)
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(name, "done in", out["oracle_seconds"], "s", flush=True)
+
+
+if __name__ == "__main__":
+    for t in sys.argv[1:]:
+        run(t)

@@ -1,0 +1,148 @@
+"""GPU parity of Algorithm 4, the inverse block, the eigenvalues and the gradient.
+
+X (first k columns of L^{-1}) must match the oracle bit for bit (same
+operations in the same order, one truncation each).  S, lambda and the
+gradient are summed in a different order on the GPU, so they are compared
+with the oracle within the tolerance the method is asked for: lambda and
+d lambda/d beta to 1e-40 relative; S entrywise to 2^-(bits/2) relative (far
+below anything that could move lambda by 1e-40).
+"""
+import json
+import os
+from fractions import Fraction
+
+import pytest
+
+mpm = pytest.importorskip("mpmath")
+
+from oracle import mpfloat as F
+from oracle import pipeline as PL
+from oracle import grad as GR
+from oracle import exact as EX
+from tests import inputs
+from tests.layout import from_arrays, to_arrays
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+LAMBDA_TOL = mpm.mpf(10) ** -40
+
+
+def gpu_mpf(s, e, m):
+    return F.to_mpf(F.from_limbs(int(s), int(e), m), mpm)
+
+
+def run_path(hk, beta, N, k, bits, mu=None, n_eig=3, grad=False):
+    h = hk.Hankel(0)
+    if mu is None:
+        h.moments(beta[0], beta[1], N, bits)
+    else:
+        s, e, m = to_arrays(mu, bits // 32)
+        h.set_moments(N, bits, s, e, m, beta[0], beta[1])
+    h.ldlt()
+    h.inv_block(k)
+    lam = h.lambda1(n_eig)
+    g = h.lambda1_grad() if grad else None
+    return h, lam, g
+
+
+def check_x(h, hk, X, N, k):
+    got = from_arrays(*h.export(hk.HK_X, 0, N * k))
+    bad = [(r, c) for r in range(N) for c in range(k) if got[r * k + c] != X[r][c]]
+    assert not bad, f"{len(bad)} X entries differ, first {bad[:5]}"
+
+
+@pytest.mark.parametrize("beta,N,k,bits", [((1, 2), 48, 8, 4096), ((1, 1), 40, 8, 2048), ((1, 2), 37, 5, 1024),
+                                            ((1, 2), 130, 16, 1024)])
+def test_path_vs_oracle(beta, N, k, bits):
+    import paper_1810_01478_gb300 as hk
+    n = bits // 32
+    ref = PL.run(Fraction(*beta), N, k, n)
+    h, lam, g = run_path(hk, beta, N, k, bits, grad=True)
+    try:
+        check_x(h, hk, ref["X"], N, k)
+        with mpm.workprec(ref["prec"]):
+            S = from_arrays(*h.export(hk.HK_S, 0, k * k))
+            tol_s = mpm.mpf(2) ** (-(32 * n) // 2)
+            for a in range(k):
+                for b in range(k):
+                    want = ref["S"][a, b]
+                    assert abs(F.to_mpf(S[a * k + b], mpm) - want) <= tol_s * abs(want)
+            s, e, m, f64, terr = lam
+            for j in range(3):
+                got = gpu_mpf(s[j], e[j], m[j])
+                assert abs(got - ref["lambdas"][j]) / ref["lambdas"][j] < LAMBDA_TOL, j
+                assert abs(f64[j] - float(ref["lambdas"][j])) <= 1e-15 * abs(f64[j])
+                assert abs(terr[j] - float(ref["trunc_errors"][j])) <= 1e-6 * abs(float(ref["trunc_errors"][j]))
+            mm = Fraction(*beta)
+            mden = mm.denominator // mm.numerator
+            gref, _, _ = GR.analytic_grad(mm, lambda s_: mden * mpm.factorial(mden * (s_ + 1) - 1), ref["L"],
+                                          ref["D"], ref["X"], k, n)
+            got_g = gpu_mpf(g[0][0], g[1][0], g[2][0])
+            assert abs(got_g - gref) / abs(gref) < LAMBDA_TOL
+    finally:
+        h.close()
+
+
+def test_full_block_is_true_smallest_eigenvalue():
+    # k = N: lambda^(N) is the smallest eigenvalue of H_N itself
+    import paper_1810_01478_gb300 as hk
+    N, bits = 16, 1024
+    h, lam, _ = run_path(hk, (1, 2), N, N, bits, n_eig=2)
+    try:
+        with mpm.workprec(1500):
+            H = mpm.matrix(N, N)
+            for i in range(N):
+                for j in range(N):
+                    H[i, j] = 2 * mpm.factorial(2 * (i + j) + 1)
+            ev = sorted(mpm.eigsy(H)[0])
+            for j in range(2):
+                got = gpu_mpf(lam[0][j], lam[1][j], lam[2][j])
+                assert abs(got - ev[j]) / ev[j] < LAMBDA_TOL
+    finally:
+        h.close()
+
+
+def test_measure_fuzz_path():
+    import paper_1810_01478_gb300 as hk
+    N, k, bits = 20, 6, 2048
+    n = bits // 32
+    mu = [F.from_int(v, n) for v in inputs.measure_moments(7, N)]
+    ref = PL.run(None, N, k, n, mu=mu)
+    h, lam, _ = run_path(hk, (0, 0), N, k, bits, mu=mu, n_eig=1)
+    try:
+        check_x(h, hk, ref["X"], N, k)
+        with mpm.workprec(ref["prec"]):
+            got = gpu_mpf(lam[0][0], lam[1][0], lam[2][0])
+            assert abs(got - ref["lambdas"][0]) / ref["lambdas"][0] < LAMBDA_TOL
+    finally:
+        h.close()
+
+
+def golden(name):
+    path = os.path.join(HERE, "golden", name + ".json")
+    if not os.path.exists(path):
+        pytest.skip(f"golden {name} not generated")
+    return json.load(open(path))
+
+
+def test_config2_and_4_against_golden():
+    """beta = 1/2, N = 256, k = 16, 8192 bits: factor and X bit for bit (digests),
+    lambda_1..3 and the gradient to 1e-40 (oracle analytic and finite difference)."""
+    import paper_1810_01478_gb300 as hk
+    from tests.digest import factor_digest, x_digest
+    gd = golden("c2")
+    N, k, bits = gd["N"], gd["k"], gd["bits"]
+    h, lam, g = run_path(hk, tuple(gd["beta"]), N, k, bits, grad=True)
+    try:
+        assert factor_digest(h, hk, N) == gd["factor_sha256"]
+        assert x_digest(h, hk, N, k) == gd["x_sha256"]
+        with mpm.workprec(2 * bits):
+            for j in range(3):
+                want = mpm.mpf(gd["lambdas"][j])
+                assert abs(gpu_mpf(lam[0][j], lam[1][j], lam[2][j]) - want) / want < LAMBDA_TOL
+            got_g = gpu_mpf(g[0][0], g[1][0], g[2][0])
+            for key in ("grad", "grad_fd"):
+                want = mpm.mpf(gd[key])
+                assert abs(got_g - want) / abs(want) < LAMBDA_TOL, key
+    finally:
+        h.close()

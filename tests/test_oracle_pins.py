@@ -213,6 +213,13 @@ def test_table2_n500():
 
 # --- a8: gradient ------------------------------------------------------------
 
+def test_psi_integer_identity_matches_digamma():
+    with mpm.workprec(600):
+        for x in [1, 2, 3, 10, 41, 200]:
+            assert abs(GR.psi(x, mpm) - mpm.digamma(x)) < mpm.mpf(2) ** -580
+        assert abs(GR.psi(Fraction(9, 4), mpm) - mpm.digamma(mpm.mpf(9) / 4)) < mpm.mpf(2) ** -580
+
+
 def test_gradient_closed_form_n2():
     # N = k = 2: lambda^(2) = lambda_min(H_2) = (m0 + m2 - sqrt((m0-m2)^2 + 4 m1^2)) / 2
     n, N, k = 12, 2, 2
