@@ -162,6 +162,28 @@ HK_API hk_status hk_div_batch(int bits, int64_t count, const int32_t* a_sign, co
                               const uint32_t* d_limbs, int32_t* out_sign, int32_t* out_exp, uint32_t* out_limbs,
                               void* cuda_stream);
 
+/* Allocation-free LDL^T (no counterpart in the paper: an interface for
+ * callers that cannot allow a library to allocate device memory, e.g. a
+ * process whose device memory belongs to one allocator or to a fixed budget).
+ * Runs the same Algorithm 1 as hk_ldlt, with the same results, but takes
+ * every byte of scratch (the pivot column, the pivot reciprocal, an error
+ * word) from one fixed 4 MiB array in device memory that the library declares;
+ * it calls no cudaMalloc/cudaFree and allocates nothing else.
+ *   mu_*:  DEVICE arrays of the 2N-1 moments (layout above), read only
+ *   f_*:   DEVICE arrays of N(N+1)/2 numbers, the packed factor as HK_FACTOR
+ *          describes it (caller-allocated), written
+ *   limit: N * (bits/32 + 2) + bits/32 + 35 <= HK_NOALLOC_SCRATCH_WORDS,
+ *          else HK_ERR_ARG (e.g. N <= 1024 at bits <= 24576)
+ * The first call on a device looks the array's address up (once per device,
+ * with that device current); make that first call before any stream capture.
+ * Every call shares the array, so calls that overlap on the GPU race: the
+ * caller serialises them.  Synchronises cuda_stream before returning and
+ * reports a non-positive pivot as HK_ERR_NOT_PD. */
+#define HK_NOALLOC_SCRATCH_WORDS (1u << 20)
+HK_API hk_status hk_ldlt_noalloc(int bits, int N, const int32_t* mu_sign, const int32_t* mu_exp,
+                                 const uint32_t* mu_limbs, int32_t* f_sign, int32_t* f_exp, uint32_t* f_limbs,
+                                 void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 # every entry point declared in include/hk.h
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
            "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
-           "hk_div_batch", "hk_set_profiling", "hk_get_profile"]
+           "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc"]
 PROFILE_FIELDS = 9
 
 
@@ -70,8 +70,9 @@ def load(path=LIB_PATH):
     L.hk_fused_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 12 + [_P]
     L.hk_div_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 9 + [_P]
     L.hk_set_profiling.argtypes = [_P, ctypes.c_int]
+    L.hk_ldlt_noalloc.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 6 + [_P]
     L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
-    for name in ("hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
+    for name in ("hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
                  "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -188,6 +189,17 @@ def hk_get_profile(ctx):
     keys = ["launches", "trailing_ms", "trailing_launches", "trailing_limb_macs", "moments_ms", "ldlt_ms",
             "invblock_ms", "eig_ms", "grad_ms"]
     return dict(zip(keys, out.tolist()))
+
+
+def hk_ldlt_noalloc(bits, N, mu, factor, stream=None):
+    """LDL^T into a caller-allocated factor without any device allocation.
+
+    mu: (sign_ptr, exp_ptr, limbs_ptr) device addresses of the 2N-1 moments;
+    factor: the same for N(N+1)/2 numbers (written).  For callers that cannot
+    let the library allocate device memory; see include/hk.h for the scratch
+    limit and the rule that overlapping calls race."""
+    args = [_P(p) for t in (mu, factor) for p in t]
+    _check(load().hk_ldlt_noalloc(bits, N, *args, _P(stream or 0)), what="hk_ldlt_noalloc")
 
 
 # --- layout helpers (host-side marshalling) ---------------------------------

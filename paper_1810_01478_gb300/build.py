@@ -54,7 +54,7 @@ def build(verbose=False, jobs=None):
         return LIB
     cc = nvcc()
     jobs = jobs or max(2, os.cpu_count() or 2)
-    units = [("hk_abi", os.path.join(CSRC, "hk_abi.cu"), [])]
+    units = [("hk_abi", os.path.join(CSRC, "hk_abi.cu"), []), ("hk_noalloc", os.path.join(CSRC, "hk_noalloc.cu"), [])]
     units += [(f"inst_m{m}", os.path.join(CSRC, "inst.cu"), [f"-DHK_M={m}"]) for m in widths()]
 
     def compile_one(u):

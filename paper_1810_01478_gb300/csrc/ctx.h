@@ -72,6 +72,9 @@ struct OpsTable {
   hk_status (*grad)(Ctx&, int32_t* sgn, int32_t* exp, uint32_t* mant, double* f64);
   cudaError_t (*fused_batch)(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count, cudaStream_t s);
   cudaError_t (*div_batch)(MPVec a, MPVec d, MPVec out, int64_t count, int* err, cudaStream_t s);
+  // Algorithm 1 on caller-provided buffers (no allocation): see hk_ldlt_noalloc
+  cudaError_t (*ldlt_raw)(MPVec mu, MPVec A, MPVec U, uint32_t* rec, int* rec_meta, int* err, int N,
+                          cudaStream_t s, int device);
 };
 
 const OpsTable* ops_for(int M);

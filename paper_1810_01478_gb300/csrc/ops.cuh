@@ -112,12 +112,43 @@ struct Ops {
     return check_cuda(c, cudaGetLastError(), "launching the factorisation");
   }
 
+  // The same launch sequence as ldlt() on buffers the caller provides
+  // (hk_ldlt_noalloc): mu (2N-1), A (packed factor), U (N), rec (n limbs),
+  // rec_meta and err (device ints).  Launches only; allocates nothing.
+  static cudaError_t ldlt_raw(MPVec mu, MPVec A, MPVec U, uint32_t* rec, int* rec_meta, int* err, int N,
+                              cudaStream_t s, int device) {
+    cudaError_t e;
+    if ((e = allow_smem(k_trailing<M>, fused_smem)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_scale<M>, div_smem)) != cudaSuccess) return e;
+    if ((e = allow_smem(k_recip_pivot<M>, recip_smem)) != cudaSuccess) return e;
+    const int trail_res = resident_blocks(k_trailing<M>, 32 * WARPS, fused_smem, device);
+    const int scale_res = resident_blocks(k_scale<M>, 32 * WARPS, div_smem, device);
+    const int64_t tri = (int64_t)N * (N + 1) / 2;
+    {
+      const int64_t work = tri * (n / 4);
+      const int grid = (int)std::min<int64_t>((work + 255) / 256, 8 * sm_count(device) * 8);
+      k_assemble<M><<<grid, 256, 0, s>>>(mu, A, N);
+    }
+    for (int i = 0; i < N; ++i) {
+      k_recip_pivot<M><<<1, 32, recip_smem, s>>>(A, N, i, rec, rec_meta, err);
+      if (i == N - 1) break;
+      const int64_t rows = N - 1 - i;
+      const int gs = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, scale_res);
+      k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(A, U, N, i, rec, rec_meta, err);
+      const int64_t T = rows * (rows + 1) / 2;
+      const int gt = (int)std::min<int64_t>((T + WARPS - 1) / WARPS, trail_res);
+      k_trailing<M><<<gt, 32 * WARPS, fused_smem, s>>>(A, U, N, i, 0, T, err);
+    }
+    return cudaGetLastError();
+  }
+
   static hk_status inv_block(Ctx& c);
   static hk_status lambda(Ctx& c, int n_eig);
   static hk_status grad(Ctx& c, int32_t* sgn, int32_t* exp, uint32_t* mant, double* f64);
 
   static OpsTable table() {
-    return OpsTable{M, &Ops::ldlt, &Ops::inv_block, &Ops::lambda, &Ops::grad, &Ops::fused_batch, &Ops::div_batch};
+    return OpsTable{M,           &Ops::ldlt,        &Ops::inv_block, &Ops::lambda, &Ops::grad,
+                    &Ops::fused_batch, &Ops::div_batch, &Ops::ldlt_raw};
   }
 };
 
