@@ -162,6 +162,32 @@ HK_API hk_status hk_div_batch(int bits, int64_t count, const int32_t* a_sign, co
                               const uint32_t* d_limbs, int32_t* out_sign, int32_t* out_exp, uint32_t* out_limbs,
                               void* cuda_stream);
 
+/* a9. Batched form: `count` independent instances (uneven beta, N, k, bits)
+ * solved concurrently on one device, each on its own stream and context,
+ * driven by up to `max_concurrent` host threads (0 = all at once).  Per
+ * instance: moments on the device when mu_* are NULL (beta = 1/m), else
+ * imported from the host arrays; then hk_ldlt, hk_inv_block(k) and
+ * hk_lambda1(n_eig).  Results and the instance's own status are written into
+ * its struct; the call returns HK_OK when every instance succeeded, else the
+ * first failing instance's status. */
+typedef struct hk_instance {
+  int64_t beta_num, beta_den;
+  int32_t N, k, bits, n_eig;
+  const int32_t* mu_sign;       /* host, 2N-1 moments, or NULL */
+  const int32_t* mu_exp;
+  const uint32_t* mu_limbs;
+  int32_t* lambda_sign;         /* host outputs, n_eig numbers, or NULL */
+  int32_t* lambda_exp;
+  uint32_t* lambda_limbs;
+  double lambda_f64[3];
+  double trunc_err_f64[3];
+  double seconds;               /* wall time of this instance */
+  int32_t status;
+  int32_t reserved;
+  char message[128];            /* hk_last_error of a failed instance ("" if none) */
+} hk_instance;
+HK_API hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_concurrent);
+
 /* Allocation-free LDL^T (no counterpart in the paper: an interface for
  * callers that cannot allow a library to allocate device memory, e.g. a
  * process whose device memory belongs to one allocator or to a fixed budget).

@@ -53,3 +53,42 @@ def mpf_to_format(v, n, mpm):
     # value = man * 2^exp exactly; express at a limb-aligned exponent
     e32, r = divmod(exp, 32)
     return F.rnd(int(man) << r, e32, n)
+
+
+# --- rational beta = a/b through a-1 constants --------------------------------
+# (j+1)/beta = b(j+1)/a = q + r/a with 0 <= r < a, and Gamma(q + r/a) =
+# Gamma(r/a) * prod_{i<q} (r/a + i)  (the functional equation Gamma(x+1) =
+# x Gamma(x)), so mu_j = (b/a) * Gamma(r/a) * prod_{i<q} (r + i a) / a^q, with
+# Gamma(0/a + q) = (q-1)!.  Only Gamma(1/a) .. Gamma((a-1)/a) are transcendental.
+
+def gamma_constants(beta, bits):
+    """[None, Gamma(1/a), ..., Gamma((a-1)/a)] as exact Fractions of mpmath
+    values computed at `bits` bits (beta = a/b in lowest terms)."""
+    import mpmath as mpm
+    beta = Fraction(beta)
+    a = beta.numerator
+    out = [None]
+    with mpm.workprec(bits):
+        for r in range(1, a):
+            man, exp = mpm.gamma(mpm.mpf(r) / a).man_exp
+            out.append(Fraction(int(man)) * Fraction(2) ** int(exp))
+    return out
+
+
+def moments_from_constants(beta, N, n, consts):
+    """mu_0..mu_{2N-2} for beta = a/b from the constants of gamma_constants,
+    each formed as an exact rational and truncated once to n limbs."""
+    beta = Fraction(beta)
+    a, b = beta.numerator, beta.denominator
+    mus = []
+    for j in range(2 * N - 1):
+        q, r = divmod(b * (j + 1), a)
+        if r == 0:
+            v = Fraction(b, a) * factorial(q - 1)
+        else:
+            num = b
+            for i in range(q):
+                num *= r + i * a
+            v = Fraction(num, a ** (q + 1)) * consts[r]
+        mus.append(F.from_fraction(v, n))
+    return mus

@@ -27,7 +27,18 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 # every entry point declared in include/hk.h
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
            "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
-           "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc"]
+           "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run"]
+
+
+class Instance(ctypes.Structure):
+    """hk_instance of include/hk.h (one problem of hk_batch_run)."""
+    _fields_ = [("beta_num", ctypes.c_int64), ("beta_den", ctypes.c_int64), ("N", ctypes.c_int32),
+                ("k", ctypes.c_int32), ("bits", ctypes.c_int32), ("n_eig", ctypes.c_int32),
+                ("mu_sign", ctypes.c_void_p), ("mu_exp", ctypes.c_void_p), ("mu_limbs", ctypes.c_void_p),
+                ("lambda_sign", ctypes.c_void_p), ("lambda_exp", ctypes.c_void_p), ("lambda_limbs", ctypes.c_void_p),
+                ("lambda_f64", ctypes.c_double * 3), ("trunc_err_f64", ctypes.c_double * 3),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("message", ctypes.c_char * 128)]
 PROFILE_FIELDS = 9
 
 
@@ -70,9 +81,10 @@ def load(path=LIB_PATH):
     L.hk_fused_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 12 + [_P]
     L.hk_div_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 9 + [_P]
     L.hk_set_profiling.argtypes = [_P, ctypes.c_int]
+    L.hk_batch_run.argtypes = [ctypes.c_int, ctypes.POINTER(Instance), ctypes.c_int, ctypes.c_int]
     L.hk_ldlt_noalloc.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 6 + [_P]
     L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
-    for name in ("hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
+    for name in ("hk_batch_run", "hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
                  "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -200,6 +212,45 @@ def hk_ldlt_noalloc(bits, N, mu, factor, stream=None):
     limit and the rule that overlapping calls race."""
     args = [_P(p) for t in (mu, factor) for p in t]
     _check(load().hk_ldlt_noalloc(bits, N, *args, _P(stream or 0)), what="hk_ldlt_noalloc")
+
+
+def hk_batch_run(device, problems, max_concurrent=0):
+    """Solve several instances concurrently.  problems: list of dicts with
+    beta (num, den), N, k, bits, n_eig and optional mu = (sign, exp, limbs)
+    host arrays.  Returns a list of dicts (status, lambda_f64, trunc_err_f64,
+    lambda = (sign, exp, limbs), seconds) in the same order."""
+    arr = (Instance * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        it = arr[i]
+        it.beta_num, it.beta_den = p["beta"]
+        it.N, it.k, it.bits, it.n_eig = p["N"], p["k"], p["bits"], p.get("n_eig", 1)
+        n = p["bits"] // 32
+        if p.get("mu") is not None:
+            s, e, m = (np.ascontiguousarray(p["mu"][0], np.int32), np.ascontiguousarray(p["mu"][1], np.int32),
+                       np.ascontiguousarray(p["mu"][2], np.uint32))
+            keep += [s, e, m]
+            it.mu_sign, it.mu_exp, it.mu_limbs = s.ctypes.data, e.ctypes.data, m.ctypes.data
+        ls = np.zeros(it.n_eig, np.int32)
+        le = np.zeros(it.n_eig, np.int32)
+        lm = np.zeros((it.n_eig, n), np.uint32)
+        keep += [ls, le, lm]
+        it.lambda_sign, it.lambda_exp, it.lambda_limbs = ls.ctypes.data, le.ctypes.data, lm.ctypes.data
+    st = load().hk_batch_run(device, arr, len(problems), max_concurrent)
+    out = []
+    for i in range(len(problems)):
+        it = arr[i]
+        out.append(dict(status=it.status, message=it.message.decode(errors="replace"),
+                        lambda_f64=list(it.lambda_f64)[:it.n_eig],
+                        trunc_err_f64=list(it.trunc_err_f64)[:it.n_eig], seconds=it.seconds))
+    # lambda arrays in problem order (the last three kept arrays of each problem)
+    j = 0
+    for i, p in enumerate(problems):
+        if p.get("mu") is not None:
+            j += 3
+        out[i]["lambda"] = (keep[j], keep[j + 1], keep[j + 2])
+        j += 3
+    return st, out
 
 
 # --- layout helpers (host-side marshalling) ---------------------------------

@@ -45,13 +45,19 @@ def _sources_digest():
     return h.hexdigest()
 
 
-def build(verbose=False, jobs=None):
-    """Compile libhk.so unless an up-to-date one exists; returns its path."""
-    os.makedirs(OUT, exist_ok=True)
-    digest = _sources_digest()
-    stamp = os.path.join(OUT, "libhk.digest")
-    if os.path.exists(LIB) and os.path.exists(stamp) and open(stamp).read() == digest:
-        return LIB
+def build(verbose=False, jobs=None, out_dir=None, defines=()):
+    """Compile libhk.so unless an up-to-date one exists; returns its path.
+
+    out_dir / defines: an alternative build directory and extra -D flags
+    (used to compare kernel variants side by side)."""
+    out = out_dir or OUT
+    lib = os.path.join(out, "libhk.so")
+    os.makedirs(out, exist_ok=True)
+    extra_flags = ["-D" + d for d in defines]
+    digest = _sources_digest() + " ".join(extra_flags)
+    stamp = os.path.join(out, "libhk.digest")
+    if os.path.exists(lib) and os.path.exists(stamp) and open(stamp).read() == digest:
+        return lib
     cc = nvcc()
     jobs = jobs or max(2, os.cpu_count() or 2)
     units = [("hk_abi", os.path.join(CSRC, "hk_abi.cu"), []), ("hk_noalloc", os.path.join(CSRC, "hk_noalloc.cu"), [])]
@@ -59,8 +65,8 @@ def build(verbose=False, jobs=None):
 
     def compile_one(u):
         name, src, extra = u
-        obj = os.path.join(OUT, name + ".o")
-        cmd = [cc] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
+        obj = os.path.join(out, name + ".o")
+        cmd = [cc] + ARCH + FLAGS + extra_flags + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {name}:\n{r.stderr}")
@@ -72,15 +78,15 @@ def build(verbose=False, jobs=None):
     units.sort(key=lambda u: -int(u[2][0].split("=")[1]) if u[2] else 0)
     with ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(compile_one, units))
-    tmp = LIB + ".tmp"
-    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    tmp = lib + ".tmp"
+    cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(digest)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

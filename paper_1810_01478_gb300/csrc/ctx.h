@@ -39,6 +39,10 @@ struct Ctx {
   DevVec mu, A, U, X, S, evec, scratch;
   uint32_t* rec = nullptr;    // pivot reciprocal scratch (n limbs)
   int* rec_meta = nullptr;
+  // look-ahead: the next pivot's reciprocal runs on `aux` while the main
+  // stream finishes the current trailing update (Alg. 2's look-ahead, Sec. 4.3.1)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_diag = nullptr, ev_recip = nullptr;
   // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
   std::map<std::string, DevVec> pool;
   void* d_tasks = nullptr;    // task descriptors of the current launch

@@ -1,8 +1,12 @@
 // The C ABI of libhk (declared in include/hk.h): context management, call-order
 // enforcement, host <-> device transfers and dispatch to the per-width launchers.
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 
 #include "ctx.h"
 #include "k_moments.cuh"
@@ -171,6 +175,9 @@ void hk_destroy(hk_ctx* h) {
   for (auto& kv : c.pool) dev_free(kv.second);
   if (c.d_tasks) cudaFree(c.d_tasks);
   for (cudaEvent_t e : c.events) cudaEventDestroy(e);
+  if (c.ev_diag) cudaEventDestroy(c.ev_diag);
+  if (c.ev_recip) cudaEventDestroy(c.ev_recip);
+  if (c.aux) cudaStreamDestroy(c.aux);
   if (c.rec) cudaFree(c.rec);
   if (c.d_err) cudaFree(c.d_err);
   delete h;
@@ -211,9 +218,12 @@ hk_status hk_moments(hk_ctx* h, int64_t beta_num, int64_t beta_den, int N, int b
   const double bits_needed = (std::lgamma(top) + std::log((double)m)) / std::log(2.0) + 96.0;
   int64_t cap = ((int64_t)(bits_needed / 32.0) + 2 + 31) / 32 * 32;
   if (cap < 64) cap = 64;
-  if (cap * 4 > 200 * 1024) return set_error(c, HK_ERR_UNSUPPORTED, "moments too long for the exact kernel");
+  constexpr int kMomentsSmemCap = 200 * 1024;
+  if (cap * 4 > kMomentsSmemCap) return set_error(c, HK_ERR_UNSUPPORTED, "moments too long for the exact kernel");
+  // the attribute is process-wide: always set the same (maximal) cap, so that
+  // contexts working concurrently never lower it under each other's launches
   if ((st = check_cuda(c, cudaFuncSetAttribute(k_moments_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(cap * 4)),
+                                               kMomentsSmemCap),
                        "smem attribute")) != HK_OK)
     return st;
   const size_t pe0 = c.prof ? prof_mark(c) : 0;
@@ -385,6 +395,58 @@ hk_status hk_get_profile(hk_ctx* h, double* out, int cap) {
     cudaEventElapsedTime(&ms, c.events[p.second.first], c.events[p.second.second]);
     out[4 + p.first] += ms;
   }
+  return HK_OK;
+}
+
+static void run_instance(int device, hk_instance& in) {
+  const auto t0 = std::chrono::steady_clock::now();
+  hk_status st = HK_OK;
+  cudaStream_t s = nullptr;
+  hk_ctx* h = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    in.status = HK_ERR_CUDA;
+    return;
+  }
+  st = hk_create(device, s, &h);
+  if (st == HK_OK) {
+    if (in.mu_sign && in.mu_exp && in.mu_limbs)
+      st = hk_set_moments(h, in.N, in.bits, in.mu_sign, in.mu_exp, in.mu_limbs, in.beta_num, in.beta_den);
+    else
+      st = hk_moments(h, in.beta_num, in.beta_den, in.N, in.bits);
+  }
+  if (st == HK_OK) st = hk_ldlt(h);
+  if (st == HK_OK) st = hk_inv_block(h, in.k);
+  if (st == HK_OK)
+    st = hk_lambda1(h, in.n_eig, in.lambda_sign, in.lambda_exp, in.lambda_limbs, in.lambda_f64, in.trunc_err_f64);
+  in.message[0] = 0;
+  if (st != HK_OK) {
+    std::snprintf(in.message, sizeof(in.message), "%s", h ? hk_last_error(h) : "context creation failed");
+    if (!in.message[0]) std::snprintf(in.message, sizeof(in.message), "status %d", (int)st);
+  }
+  if (h) hk_destroy(h);
+  cudaStreamDestroy(s);
+  in.status = st;
+  in.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_concurrent) {
+  if (!inst || count < 0) return HK_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    hk_instance& in = inst[i];
+    if (in.N < 1 || in.k < 1 || in.k > in.N || in.n_eig < 1 || in.n_eig > 3 || in.n_eig > in.k || !valid_bits(in.bits))
+      return HK_ERR_ARG;
+    in.status = HK_OK;
+  }
+  const int workers = (max_concurrent <= 0 || max_concurrent > count) ? count : max_concurrent;
+  std::atomic<int> next(0);
+  std::vector<std::thread> pool;
+  for (int w = 0; w < workers; ++w)
+    pool.emplace_back([&]() {
+      for (int i = next++; i < count; i = next++) run_instance(device, inst[i]);
+    });
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < count; ++i)
+    if (inst[i].status != HK_OK) return (hk_status)inst[i].status;
   return HK_OK;
 }
 

@@ -35,7 +35,7 @@ __device__ __forceinline__ Result fused_staged(const WarpSmem<M>& sm, const uint
   const bool p_zero = x_zero || y_zero;
   if (!p_zero) {
     uint32_t lo[M], hi[M];
-    warp_mul<M>(xc, sm.ys, lo, hi);
+    warp_mul<M>(xc, sm.ys, sm.sp, lo, hi);
     stage_product<M>(sm.sp, lo, hi);
     __syncwarp();
   }
@@ -206,8 +206,11 @@ __global__ void k_scale(MPVec A, MPVec U, int N, int i, const uint32_t* rec, con
 // One warp per entry; entries enumerated column by column so consecutive
 // warps share U[c].
 // ---------------------------------------------------------------------------
+#ifndef HK_TRAIL_MIN_BLOCKS
+#define HK_TRAIL_MIN_BLOCKS 3  // resident blocks of 4 warps per SM the register budget is sized for
+#endif
 template <int M>
-__global__ void __launch_bounds__(128) k_trailing(MPVec A, MPVec U, int N, int i, int64_t t0, int64_t t1,
+__global__ void __launch_bounds__(128, HK_TRAIL_MIN_BLOCKS) k_trailing(MPVec A, MPVec U, int N, int i, int64_t t0, int64_t t1,
                                                    const int* err) {
   constexpr int n = 32 * M;
   extern __shared__ uint32_t smem[];

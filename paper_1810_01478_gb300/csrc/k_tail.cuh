@@ -304,4 +304,13 @@ static __global__ void k_argmax_diag(MPVec T, int k, int kk, int n, int* out) {
   if (lane == 0) out[0] = best;
 }
 
+// flag[0] = 1 when |D[id]| <= 2^(-32 tol) |V[iv]| (top-limb indices differ by
+// at least tol) or D[id] == 0.  One thread.
+static __global__ void k_rel_small(MPVec D, int64_t id, MPVec V, int64_t iv, int n, int tol, int* flag) {
+  if (threadIdx.x || blockIdx.x) return;
+  const bool dz = D.mant[id * n + n - 1] == 0u;
+  const bool vz = V.mant[iv * n + n - 1] == 0u;
+  flag[0] = (dz || (!vz && (int64_t)V.exp[iv] - (int64_t)D.exp[id] >= tol)) ? 1 : 0;
+}
+
 }  // namespace hk

@@ -145,17 +145,24 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
     clo[k] = 0;
     chi[k] = (lane == 31 && k == M - 1) ? 0x80000000u : 0u;
   }
-  // Newton from below: R += floor(R * floor(E / 2^(32n)) / 2^(32n-1)), E = C - D'R >= 0
+  // Newton from below: R += floor(R * floor(E / 2^(32n)) / 2^(32n-1)), E = C - D'R >= 0.
+  // The precision doubles per step, so R is kept truncated to its top w limbs
+  // (w = 4, 8, 16, ... limbs; truncation keeps R below the true value) and the
+  // two products skip R's zero limbs (warp_mul skips all-zero blocks of y).
+  // `bits` is a lower bound on R's correct bits: 40 from the double start,
+  // doubling per step while below the truncation width (32 w - 8).
+  int w = 2, bits = 40;
 #pragma unroll 1
   for (int it = 0; it < 48; ++it) {
+    w = min(n, 2 * w);
 #pragma unroll
     for (int k = 0; k < M; ++k) ys[lane * M + k] = R[k];
     __syncwarp();
     uint32_t plo[M], phi[M], elo[M], ehi[M];
-    warp_mul<M>(dp, ys, plo, phi);
+    warp_mul<M>(dp, ys, sp, plo, phi);
     dsub<M>(clo, chi, plo, phi, elo, ehi);  // E >= 0 while R <= floor(C/D')
     uint32_t qlo[M], qhi[M];
-    warp_mul<M>(ehi, ys, qlo, qhi);          // (E >> 32n) * R
+    warp_mul<M>(ehi, ys, sp, qlo, qhi);          // (E >> 32n) * R
     // corr = floor(Q / 2^(32n-1)) = (Q >> (32n)) * 2 + top bit of Q's limb n-1
     uint32_t corr[M];
     {
@@ -168,12 +175,21 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
       }
     }
     __syncwarp();
-    if (!__any_sync(FULL, !chunk_is_zero<M>(corr))) break;
+    const bool done = (w == n) && !__any_sync(FULL, !chunk_is_zero<M>(corr));
+    if (done) break;
     if (nadd<M>(R, corr)) {
 #pragma unroll
       for (int k = 0; k < M; ++k) R[k] = 0xffffffffu;
       break;
     }
+    bits = min(2 * bits, 32 * w - 8);
+    if (w < n) {  // keep the top w limbs
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (lane * M + k < n - w) R[k] = 0;
+    }
+    // the exact correction below removes the last few units
+    if (w == n && bits >= 32 * n - 8) break;
     if (it == 47 && lane == 0) atomicOr(err, ERR_LOOP);
   }
   // exact correction: while C - D'R >= D': R += 1
@@ -183,7 +199,7 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
     for (int k = 0; k < M; ++k) ys[lane * M + k] = R[k];
     __syncwarp();
     uint32_t plo[M], phi[M], elo[M], ehi[M];
-    warp_mul<M>(dp, ys, plo, phi);
+    warp_mul<M>(dp, ys, sp, plo, phi);
     const bool negative = dsub<M>(clo, chi, plo, phi, elo, ehi);
     __syncwarp();
     if (negative) {  // cannot happen when R stays below the true value
@@ -212,7 +228,7 @@ __device__ void warp_quot(const uint32_t (&a)[M], const uint32_t (&d)[M], const 
   const int lane = lane_id();
   t = (ncmp<M>(a, d) >= 0) ? n - 1 : n;
   uint32_t plo[M], phi[M];
-  warp_mul<M>(a, ys_R, plo, phi);
+  warp_mul<M>(a, ys_R, sp, plo, phi);
   // Q~ = floor(A*R / 2^shift), shift = 64n - 1 - 32t - sh
   const int shift = 64 * n - 1 - 32 * t - sh;
 #pragma unroll
@@ -229,7 +245,7 @@ __device__ void warp_quot(const uint32_t (&a)[M], const uint32_t (&d)[M], const 
   for (int k = 0; k < M; ++k) ys_tmp[lane * M + k] = d[k];
   __syncwarp();
   uint32_t qlo[M], qhi[M];
-  warp_mul<M>(q, ys_tmp, qlo, qhi);
+  warp_mul<M>(q, ys_tmp, sp, qlo, qhi);
   // A * 2^(32t) as (lo, hi): stage A at limb offset t
 #pragma unroll
   for (int k = 0; k < M; ++k) {

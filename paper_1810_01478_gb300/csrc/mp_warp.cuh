@@ -190,9 +190,14 @@ __device__ __forceinline__ void mac_row(uint32_t (&acc)[M + 1], const uint32_t (
 // block, so the buffer for chunk c collects the contributions of lanes
 // c, c-1, ... in turn and is complete when it reaches lane 0 (c < 32) or after
 // the last block (c >= 32).  Carry words ride along and are resolved at the end.
+//
+// lo_stage: n + 32 words of this warp's shared memory; the finished low
+// chunks (and their carry words) are parked there during the loop instead of
+// in registers, which keeps the loop's register footprint at about 4M words.
 template <int M>
-__device__ __forceinline__ void warp_mul(const uint32_t (&x)[M], const uint32_t* ys,
+__device__ __forceinline__ void warp_mul(const uint32_t (&x)[M], const uint32_t* ys, uint32_t* lo_stage,
                                          uint32_t (&lo)[M], uint32_t (&hi)[M]) {
+  constexpr int n = 32 * M;
   const int lane = lane_id();
   uint32_t acc[M + 1];
   uint32_t buf[M];
@@ -200,35 +205,43 @@ __device__ __forceinline__ void warp_mul(const uint32_t (&x)[M], const uint32_t*
 #pragma unroll
   for (int k = 0; k <= M; ++k) acc[k] = 0;
 #pragma unroll
-  for (int k = 0; k < M; ++k) { buf[k] = 0; lo[k] = 0; }
+  for (int k = 0; k < M; ++k) buf[k] = 0;
 
 #pragma unroll 1
   for (int q = 0; q < 32; ++q) {
     uint32_t out[M];
     const uint32_t* yq = ys + q * M;
+    uint32_t any = 0;
 #pragma unroll
-    for (int jj = 0; jj < M; ++jj) {
-      const uint32_t y = yq[jj];
-      mac_row<M>(acc, x, y);
-      out[jj] = acc[0];
+    for (int jj = 0; jj < M; ++jj) any |= yq[jj];
+    if (any) {
 #pragma unroll
-      for (int k = 0; k < M; ++k) acc[k] = acc[k + 1];
-      acc[M] = 0;
+      for (int jj = 0; jj < M; ++jj) {
+        const uint32_t y = yq[jj];
+        mac_row<M>(acc, x, y);
+        out[jj] = acc[0];
+#pragma unroll
+        for (int k = 0; k < M; ++k) acc[k] = acc[k + 1];
+        acc[M] = 0;
+      }
+    } else {
+      // an all-zero block of y adds nothing: the window only moves on by M words
+#pragma unroll
+      for (int jj = 0; jj < M; ++jj) out[jj] = acc[jj];
+      acc[0] = acc[M];
+#pragma unroll
+      for (int k = 1; k <= M; ++k) acc[k] = 0;
     }
     // buf += out
     asm volatile("add.cc.u32 %0, %0, %1;" : "+r"(buf[0]) : "r"(out[0]));
 #pragma unroll
     for (int k = 1; k < M; ++k) asm volatile("addc.cc.u32 %0, %0, %1;" : "+r"(buf[k]) : "r"(out[k]));
     asm volatile("addc.u32 %0, %0, 0;" : "+r"(bufc));
-    // lane 0 now holds the finished chunk q: hand it to lane q
+    // lane 0 now holds the finished chunk q: park it in shared memory
+    if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      const uint32_t v = __shfl_sync(FULL, buf[k], 0);
-      if (lane == q) lo[k] = v;
-    }
-    {
-      const uint32_t v = __shfl_sync(FULL, bufc, 0);
-      if (lane == q) loc = v;
+      for (int k = 0; k < M; ++k) lo_stage[q * M + k] = buf[k];
+      lo_stage[n + q] = bufc;
     }
     // move every buffer one lane down; lane 31 starts a fresh chunk
 #pragma unroll
@@ -239,6 +252,11 @@ __device__ __forceinline__ void warp_mul(const uint32_t (&x)[M], const uint32_t*
     bufc = __shfl_down_sync(FULL, bufc, 1);
     if (lane == 31) bufc = 0;
   }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < M; ++k) lo[k] = lo_stage[lane * M + k];
+  loc = lo_stage[n + lane];
+  __syncwarp();
   // lane l: buf = chunk l+32 from lanes l+1..31, acc[0..M) = top of Z_l (chunk l+32)
   {
     uint32_t top[M];

@@ -11,7 +11,10 @@ namespace hk {
 
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+  // prefer the largest shared-memory carveout so that shared memory does not
+  // cap the number of resident blocks below what registers allow
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e != cudaSuccess || bytes <= 48 * 1024) return e;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -85,30 +88,55 @@ struct Ops {
     const int trail_res = resident_blocks(k_trailing<M>, 32 * WARPS, fused_smem, c.device);
     const int scale_res = resident_blocks(k_scale<M>, 32 * WARPS, div_smem, c.device);
     cudaStream_t s = c.stream;
+    if (!c.aux) {
+      if ((st = check_cuda(c, cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking), "aux stream")) ||
+          (st = check_cuda(c, cudaEventCreateWithFlags(&c.ev_diag, cudaEventDisableTiming), "event")) ||
+          (st = check_cuda(c, cudaEventCreateWithFlags(&c.ev_recip, cudaEventDisableTiming), "event")))
+        return st;
+    }
     {
       const int64_t work = tri * (n / 4);
       const int grid = (int)std::min<int64_t>((work + 255) / 256, 8 * sm_count(c.device) * 8);
       k_assemble<M><<<grid, 256, 0, s>>>(c.mu.view(), c.A.view(), N);
       count_launch(c);
     }
-    for (int i = 0; i < N; ++i) {
-      k_recip_pivot<M><<<1, 32, recip_smem, s>>>(c.A.view(), N, i, c.rec, c.rec_meta, c.d_err);
-      count_launch(c);
-      if (i == N - 1) break;
+    // reciprocal of d_0 on the auxiliary stream
+    cudaEventRecord(c.ev_diag, s);
+    cudaStreamWaitEvent(c.aux, c.ev_diag, 0);
+    k_recip_pivot<M><<<1, 32, recip_smem, c.aux>>>(c.A.view(), N, 0, c.rec, c.rec_meta, c.d_err);
+    cudaEventRecord(c.ev_recip, c.aux);
+    count_launch(c);
+    for (int i = 0; i < N - 1; ++i) {
       const int64_t rows = N - 1 - i;
+      const int64_t T = rows * (rows + 1) / 2;
+      cudaStreamWaitEvent(s, c.ev_recip, 0);  // R_i is ready
       const int gs = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, scale_res);
       k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(c.A.view(), c.U.view(), N, i, c.rec, c.rec_meta, c.d_err);
-      const int64_t m = rows;
-      const int64_t T = m * (m + 1) / 2;
-      const int gt = (int)std::min<int64_t>((T + WARPS - 1) / WARPS, trail_res);
+      // look-ahead: update d_{i+1} = A[i+1][i+1] first (entry t = 0 of the trailing triangle) ...
       const size_t e0 = c.prof ? prof_mark(c) : 0;
-      k_trailing<M><<<gt, 32 * WARPS, fused_smem, s>>>(c.A.view(), c.U.view(), N, i, 0, T, c.d_err);
+      k_trailing<M><<<1, 32 * WARPS, fused_smem, s>>>(c.A.view(), c.U.view(), N, i, 0, 1, c.d_err);
       if (c.prof) {
         c.trail_ev.push_back({e0, prof_mark(c)});
-        c.trail_macs += (double)T * n * n;  // n^2 limb products per fused operation
+        c.trail_macs += (double)n * n;
       }
-      count_launch(c, 2);
+      // ... start its reciprocal on the auxiliary stream ...
+      cudaEventRecord(c.ev_diag, s);
+      cudaStreamWaitEvent(c.aux, c.ev_diag, 0);
+      k_recip_pivot<M><<<1, 32, recip_smem, c.aux>>>(c.A.view(), N, i + 1, c.rec, c.rec_meta, c.d_err);
+      cudaEventRecord(c.ev_recip, c.aux);
+      // ... while the main stream updates the rest of the trailing triangle
+      if (T > 1) {
+        const int gt = (int)std::min<int64_t>((T - 1 + WARPS - 1) / WARPS, trail_res);
+        const size_t e1 = c.prof ? prof_mark(c) : 0;
+        k_trailing<M><<<gt, 32 * WARPS, fused_smem, s>>>(c.A.view(), c.U.view(), N, i, 1, T, c.d_err);
+        if (c.prof) {
+          c.trail_ev.push_back({e1, prof_mark(c)});
+          c.trail_macs += (double)(T - 1) * n * n;  // n^2 limb products per fused operation
+        }
+      }
+      count_launch(c, T > 1 ? 4 : 3);
     }
+    cudaStreamWaitEvent(s, c.ev_recip, 0);  // the last pivot's check belongs to this call
     return check_cuda(c, cudaGetLastError(), "launching the factorisation");
   }
 

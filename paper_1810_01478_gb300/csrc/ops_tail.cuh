@@ -198,30 +198,18 @@ struct Tail {
   // ------------------------------------------------------------------------
   // T = Sm^(2^s) by repeated squaring (T -> nu_1^(2^s) u u^T), v = the column
   // of T with the largest diagonal entry, nu = v^T Sm v / v^T v (Rayleigh
-  // quotient, error ~ (nu_2/nu_1)^(2^(s+1))).  Writes v (kk numbers) into V
-  // and nu, v^T v into scal[slot], scal[slot + 1].
-  static hk_status eig_top(Ctx& c, MPVec Sm, int k, int kk, int s, MPVec V, DevVec& scal, int slot) {
-    DevVec* T0 = pool_get(c, "T0", (int64_t)k * k);
-    DevVec* T1 = pool_get(c, "T1", (int64_t)k * k);
+  // quotient, error ~ (nu_2/nu_1)^(2^(s+1))).  After s0 squarings it keeps
+  // squaring until two successive quotients agree to `tol` limbs (at most 40
+  // squarings).  Writes v (kk numbers) into V and nu, v^T v into scal[slot],
+  // scal[slot + 1].
+  static hk_status rayleigh(Ctx& c, MPVec Sm, MPVec T, int k, int kk, MPVec V, DevVec& scal, int slot) {
     DevVec* Wv = pool_get(c, "w", k);
     DevVec* Rs = pool_get(c, "recip_s", 4);
-    if (!T0 || !T1 || !Wv || !Rs) return c.sticky;
+    DevVec* tmp = pool_get(c, "eig_tmp", 2);
+    if (!Wv || !Rs || !tmp) return c.sticky;
     hk_status st;
-    std::vector<ChainTask> cp;
-    for (int a = 0; a < kk; ++a)
-      for (int b = 0; b < kk; ++b)
-        cp.push_back(ChainTask{(int64_t)a * k + b, (int64_t)a * k + b, 0, 0, 0, 0, 0, 0});
-    if ((st = chains(c, cp, Sm, Sm, Sm, T0->view())) != HK_OK) return st;
-    for (int it = 0; it < s; ++it) {
-      std::vector<Dot> sq;
-      for (int a = 0; a < kk; ++a)
-        for (int b = 0; b < kk; ++b)
-          sq.push_back(Dot{(int64_t)a * k + b, (int64_t)a * k, b, 1, k, kk, false});
-      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view())) != HK_OK) return st;
-      std::swap(*T0, *T1);
-    }
     int* d_j = c.d_err + 4;
-    k_argmax_diag<<<1, 32, 0, c.stream>>>(T0->view(), k, kk, n, d_j);
+    k_argmax_diag<<<1, 32, 0, c.stream>>>(T, k, kk, n, d_j);
     count_launch(c);
     int j = 0;
     if ((st = check_cuda(c, cudaMemcpyAsync(&j, d_j, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "argmax")) ||
@@ -229,19 +217,61 @@ struct Tail {
       return st;
     std::vector<ChainTask> col;
     for (int a = 0; a < kk; ++a) col.push_back(ChainTask{a, (int64_t)a * k + j, 0, 0, 0, 0, 0, 0});
-    if ((st = chains(c, col, T0->view(), T0->view(), T0->view(), V)) != HK_OK) return st;
+    if ((st = chains(c, col, T, T, T, V)) != HK_OK) return st;
     std::vector<Dot> sv;
     for (int a = 0; a < kk; ++a) sv.push_back(Dot{a, (int64_t)a * k, 0, 1, 1, kk, false});
     if ((st = dots(c, sv, Sm, V, Wv->view())) != HK_OK) return st;
-    DevVec* tmp = pool_get(c, "eig_tmp", 2);
-    if (!tmp) return c.sticky;
     if ((st = dots(c, {Dot{0, 0, 0, 1, 1, kk, false}}, V, Wv->view(), tmp->view())) != HK_OK) return st;
     if ((st = dots(c, {Dot{1, 0, 0, 1, 1, kk, false}}, V, V, tmp->view())) != HK_OK) return st;
     if ((st = recips(c, tmp->view(), {1}, *Rs)) != HK_OK) return st;
-    // nu = num / den;  copy den
     if ((st = quots(c, {QuotTask{slot, 0, 1, 0, 0, 0}}, tmp->view(), tmp->view(), *Rs, scal.view())) != HK_OK)
       return st;
     return chains(c, {ChainTask{slot + 1, 1, 0, 0, 0, 0, 0, 0}}, tmp->view(), tmp->view(), tmp->view(), scal.view());
+  }
+
+  static hk_status eig_top(Ctx& c, MPVec Sm, int k, int kk, int s0, int tol, MPVec V, DevVec& scal, int slot) {
+    DevVec* T0 = pool_get(c, "T0", (int64_t)k * k);
+    DevVec* T1 = pool_get(c, "T1", (int64_t)k * k);
+    DevVec* ONE = one(c);
+    if (!T0 || !T1 || !ONE) return c.sticky;
+    hk_status st;
+    std::vector<ChainTask> cp;
+    for (int a = 0; a < kk; ++a)
+      for (int b = 0; b < kk; ++b)
+        cp.push_back(ChainTask{(int64_t)a * k + b, (int64_t)a * k + b, 0, 0, 0, 0, 0, 0});
+    if ((st = chains(c, cp, Sm, Sm, Sm, T0->view())) != HK_OK) return st;
+    std::vector<Dot> sq;
+    for (int a = 0; a < kk; ++a)
+      for (int b = 0; b < kk; ++b) sq.push_back(Dot{(int64_t)a * k + b, (int64_t)a * k, b, 1, k, kk, false});
+    for (int it = 0; it < s0; ++it) {
+      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view())) != HK_OK) return st;
+      std::swap(*T0, *T1);
+    }
+    if ((st = rayleigh(c, Sm, T0->view(), k, kk, V, scal, slot)) != HK_OK) return st;
+    // keep squaring until the quotient is stable: nu' - nu small against nu
+    const int pslot = slot + 8;  // scal[pslot], scal[pslot + 1]: the next quotient
+    int* flag = c.d_err + 8;
+    for (int it = s0; it < 40; ++it) {
+      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view())) != HK_OK) return st;
+      std::swap(*T0, *T1);
+      if ((st = rayleigh(c, Sm, T0->view(), k, kk, V, scal, pslot)) != HK_OK) return st;
+      // scal[pslot + 2] = nu' - 1 * nu
+      if ((st = chains(c, {ChainTask{pslot + 2, pslot, 0, slot, 0, 0, 1, 0}}, ONE->view(), scal.view(),
+                       scal.view(), scal.view())) != HK_OK)
+        return st;
+      k_rel_small<<<1, 32, 0, c.stream>>>(scal.view(), pslot + 2, scal.view(), pslot, n, tol, flag);
+      count_launch(c);
+      int close = 0;
+      if ((st = check_cuda(c, cudaMemcpyAsync(&close, flag, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "flag")) ||
+          (st = check_cuda(c, cudaStreamSynchronize(c.stream), "flag sync")))
+        return st;
+      // adopt the newer quotient either way
+      if ((st = chains(c, {ChainTask{slot, pslot, 0, 0, 0, 0, 0, 0}, ChainTask{slot + 1, pslot + 1, 0, 0, 0, 0, 0, 0}},
+                       scal.view(), scal.view(), scal.view(), scal.view())) != HK_OK)
+        return st;
+      if (close) return HK_OK;
+    }
+    return set_error(c, HK_ERR_PRECISION, "block eigenvalue did not converge in 40 squarings");
   }
 
   // Sm <- Sm - (nu / v^T v) v v^T on the leading kk block (removes nu from the spectrum)
@@ -265,14 +295,15 @@ struct Tail {
   }
 
   static int squarings_for(int bits_target) {
-    // (nu_2/nu_1)^(2^(s+1)) < 2^-bits_target when nu_2/nu_1 <= 1/2
+    // (nu_2/nu_1)^(2^(s+1)) < 2^-bits_target when nu_2/nu_1 <= 1/2; eig_top
+    // squares further if the quotient has not settled
     int s = 1;
     while ((1 << (s + 1)) < bits_target) ++s;
-    return s + 2;
+    return s;
   }
 
   // eigenvalues of the leading kk block: lam[m] = 1/nu_m (m < ne) into LAM[m]
-  static hk_status block_lambdas(Ctx& c, int kk, int ne, int s, MPVec LAM, bool keep_vector) {
+  static hk_status block_lambdas(Ctx& c, int kk, int ne, int s, int tol, MPVec LAM, bool keep_vector) {
     const int k = c.k;
     DevVec* Sw = pool_get(c, "Sw", (int64_t)k * k);
     DevVec* V = pool_get(c, "v", k);
@@ -285,7 +316,7 @@ struct Tail {
     for (int64_t e = 0; e < (int64_t)k * k; ++e) cp.push_back(ChainTask{e, e, 0, 0, 0, 0, 0, 0});
     if ((st = chains(c, cp, c.S.view(), c.S.view(), c.S.view(), Sw->view())) != HK_OK) return st;
     for (int m = 0; m < ne; ++m) {
-      if ((st = eig_top(c, Sw->view(), k, kk, s, V->view(), *scal, 2 * m)) != HK_OK) return st;
+      if ((st = eig_top(c, Sw->view(), k, kk, s, tol, V->view(), *scal, 2 * m)) != HK_OK) return st;
       if (m == 0 && keep_vector) {
         DevVec* E1 = pool_get(c, "eig1", 2);  // nu_1, v^T v
         if (!E1) return c.sticky;
@@ -318,11 +349,14 @@ struct Tail {
     DevVec* LAM1 = pool_get(c, "lam_km1", 3);
     DevVec* DIF = pool_get(c, "lam_diff", 3);
     if (!LAM || !LAM1 || !DIF) return c.sticky;
-    if ((st = block_lambdas(c, k, n_eig, squarings_for(32 * n + 64), LAM->view(), true)) != HK_OK) return st;
+    // lambda to the working precision (agreement to n - 3 limbs) ...
+    if ((st = block_lambdas(c, k, n_eig, squarings_for(32 * n + 64), n - 3, LAM->view(), true)) != HK_OK) return st;
     const int ne1 = std::min(n_eig, k - 1);
     if (ne1 > 0) {
       // the (k-1) x (k-1) estimate only feeds a double-precision difference
-      if ((st = block_lambdas(c, k - 1, ne1, squarings_for(640), LAM1->view(), false)) != HK_OK) return st;
+      // ... the (k-1) estimate only to ~640 bits (it feeds a double-precision difference)
+      if ((st = block_lambdas(c, k - 1, ne1, squarings_for(640), std::min(n - 3, 20), LAM1->view(), false)) != HK_OK)
+        return st;
       DevVec* ONE = one(c);
       if (!ONE) return c.sticky;
       std::vector<ChainTask> t;

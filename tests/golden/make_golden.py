@@ -12,7 +12,10 @@ asked) and stores, in tests/golden/<name>.json:
                           int32 exp, n uint32 limbs, all little endian
   x_sha256                the same for X (row major N x k)
 Usage:  python tests/golden/make_golden.py <target> [<target> ...]
-Targets: c1, c2, c5_512_4096, c5_768_4096, c5_1024_4096, c5_1024_8192
+Targets: c1, c2, c5_512_4096, c5_768_4096, c5_1024_4096, c5_1024_8192,
+         c3const (Gamma(r/a) constants for beta = 9/20, 11/20),
+         c3_<a>_<b>_<N> (one batched-config instance; beta = a/b, k = 16,
+         bits = 32 N, non-dyadic moments from the stored constants)
 """
 import hashlib
 import json
@@ -60,8 +63,71 @@ def x_digest(X, N, k, n):
     return h.hexdigest()
 
 
+C3_BETAS = [(9, 20), (1, 2), (11, 20), (1, 1)]
+C3_NS = [128, 192, 256, 384]
+C3_CONST_BITS = 32 * 384 + 128
+
+
+def c3_bits(N):
+    """Working precision of a batched instance: 32 N bits (4096 .. 12288)."""
+    return 32 * N
+
+
+def write_c3_constants():
+    from oracle import moments as OM
+    out = {}
+    for a, b in C3_BETAS:
+        if a == 1:
+            continue
+        consts = OM.gamma_constants(Fraction(a, b), C3_CONST_BITS)
+        out[f"{a}/{b}"] = [None] + [[hex(c.numerator), hex(c.denominator)] for c in consts[1:]]
+    with open(os.path.join(HERE, "c3_gamma_constants.json"), "w") as f:
+        json.dump(dict(bits=C3_CONST_BITS, source="oracle.moments.gamma_constants (mpmath Gamma(r/a))",
+                       constants=out), f)
+
+
+def load_c3_constants(beta):
+    d = json.load(open(os.path.join(HERE, "c3_gamma_constants.json")))
+    lst = d["constants"][f"{beta.numerator}/{beta.denominator}"]
+    return [None] + [Fraction(int(p, 16), int(q, 16)) for p, q in lst[1:]]
+
+
+def c3_moments(beta, N, n):
+    from oracle import moments as OM
+    if beta.numerator == 1:
+        return OM.moments(beta, N, n)
+    return OM.moments_from_constants(beta, N, n, load_c3_constants(beta))
+
+
+def run_c3(a, b, N):
+    import mpmath as mpm
+    beta = Fraction(a, b)
+    bits = c3_bits(N)
+    n = bits // 32
+    k = 16
+    t0 = time.time()
+    mu = c3_moments(beta, N, n)
+    r = PL.run(beta, N, k, n, mu=mu)
+    out = dict(name=f"c3_{a}_{b}_{N}", beta=[a, b], N=N, k=k, bits=bits,
+               source="tests/golden/make_golden.py (oracle only)")
+    with mpm.workprec(r["prec"]):
+        out["lambdas"] = [mpm.nstr(v, 80) for v in r["lambdas"]]
+        out["trunc_errors"] = [mpm.nstr(v, 30) for v in r["trunc_errors"]]
+        out["evals"] = [mpm.nstr(v, 30) for v in r["evals"][:4]]
+    out["factor_sha256"] = factor_digest(r["D"], r["L"], N, n)
+    out["oracle_seconds"] = round(time.time() - t0, 1)
+    with open(os.path.join(HERE, out["name"] + ".json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(out["name"], "done in", out["oracle_seconds"], "s", flush=True)
+
+
 def run(name):
     import mpmath as mpm
+    if name == "c3const":
+        return write_c3_constants()
+    if name.startswith("c3_"):
+        a, b, N = (int(v) for v in name.split("_")[1:])
+        return run_c3(a, b, N)
     cfg = TARGETS[name]
     N, k, bits = cfg["N"], cfg["k"], cfg["bits"]
     n = bits // 32

@@ -57,6 +57,19 @@ def test_moments_closed_forms_and_gamma():
             assert abs(F.to_mpf(mu[j], mpm) - v) <= F.to_mpf((1, mu[j][1]), mpm)
 
 
+def test_rational_beta_moments_from_constants():
+    # the functional-equation route agrees with mpmath's Gamma evaluated per moment
+    n = 4
+    for beta in (Fraction(9, 20), Fraction(11, 20), Fraction(3, 2)):
+        consts = M.gamma_constants(beta, 32 * n + 128)
+        mu = M.moments_from_constants(beta, 6, n, consts)
+        with mpm.workprec(32 * n + 200):
+            for j in range(11):
+                v = mpm.gamma(mpm.mpf(j + 1) * beta.denominator / beta.numerator) * beta.denominator / beta.numerator
+                assert abs(F.to_mpf(mu[j], mpm) - v) <= F.to_mpf((1, mu[j][1]), mpm)
+        assert mu == M.gamma_moments(beta, 6, n)
+
+
 # --- a3/a4: Algorithm 1 ----------------------------------------------------
 
 def test_ldlt_beta1_closed_forms():
