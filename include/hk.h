@@ -147,6 +147,20 @@ HK_API hk_status hk_export(hk_ctx* ctx, int what, int64_t first, int64_t count, 
 HK_API hk_status hk_set_profiling(hk_ctx* ctx, int on);
 HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 
+/* Exact limb products of the factorisation and of hk_fused_batch, chosen
+ * process-wide: HK_PRODUCT_SCHOOLBOOK (n^2 32x32-bit limb products, warp
+ * operand scanning), HK_PRODUCT_NTT (number-theoretic transform modulo three
+ * 31-bit primes and Chinese remaindering; the transforms of a step's pivot
+ * column are computed once and reused by every update, n <= 1024 limbs), or
+ * HK_PRODUCT_AUTO (the NTT from HK_NTT_AUTO_MIN_M * 1024 bits up).  Both give
+ * the same exact product, so results are identical bit for bit; this only
+ * changes speed.  The paper's GMP multiplies likewise switch algorithm by size. */
+#define HK_PRODUCT_AUTO 0
+#define HK_PRODUCT_SCHOOLBOOK 1
+#define HK_PRODUCT_NTT 2
+#define HK_NTT_AUTO_MIN_M 8
+HK_API hk_status hk_set_product_algorithm(int algorithm);
+
 /* Elementwise primitives on caller-owned DEVICE arrays of `count` numbers of
  * width `bits`, ordered on cuda_stream (no synchronisation):
  *   hk_fused_batch: out[i] = trunc(a[i] - x[i]*y[i])  (the update of Alg. 1/4)

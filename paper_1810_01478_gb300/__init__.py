@@ -27,7 +27,9 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 # every entry point declared in include/hk.h
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
            "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
-           "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run"]
+           "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run",
+           "hk_set_product_algorithm"]
+HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT = 0, 1, 2
 
 
 class Instance(ctypes.Structure):
@@ -81,10 +83,11 @@ def load(path=LIB_PATH):
     L.hk_fused_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 12 + [_P]
     L.hk_div_batch.argtypes = [ctypes.c_int, ctypes.c_int64] + [_P] * 9 + [_P]
     L.hk_set_profiling.argtypes = [_P, ctypes.c_int]
+    L.hk_set_product_algorithm.argtypes = [ctypes.c_int]
     L.hk_batch_run.argtypes = [ctypes.c_int, ctypes.POINTER(Instance), ctypes.c_int, ctypes.c_int]
     L.hk_ldlt_noalloc.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 6 + [_P]
     L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
-    for name in ("hk_batch_run", "hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
+    for name in ("hk_set_product_algorithm", "hk_batch_run", "hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
                  "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -188,6 +191,11 @@ def hk_fused_batch(bits, count, a, x, y, out, stream=None):
 def hk_div_batch(bits, count, a, d, out, stream=None):
     args = [_P(p) for t in (a, d, out) for p in t]
     _check(load().hk_div_batch(bits, count, *args, _P(stream or 0)), what="hk_div_batch")
+
+
+def hk_set_product_algorithm(algorithm):
+    """HK_PRODUCT_AUTO / HK_PRODUCT_SCHOOLBOOK / HK_PRODUCT_NTT (process-wide)."""
+    _check(load().hk_set_product_algorithm(algorithm), what="hk_set_product_algorithm")
 
 
 def hk_set_profiling(ctx, on=True):

@@ -8,6 +8,7 @@
 
 #include "../../include/hk.h"
 #include "common.cuh"
+#include "ntt.cuh"
 
 namespace hk {
 
@@ -43,6 +44,9 @@ struct Ctx {
   // stream finishes the current trailing update (Alg. 2's look-ahead, Sec. 4.3.1)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_diag = nullptr, ev_recip = nullptr;
+  // transforms of the current step's U and B columns (NTT products)
+  uint32_t* ntt_buf = nullptr;
+  size_t ntt_cap = 0;  // words
   // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
   std::map<std::string, DevVec> pool;
   void* d_tasks = nullptr;    // task descriptors of the current launch
@@ -87,6 +91,12 @@ const OpsTable* ops_for(int M);
 size_t prof_mark(Ctx& c);
 // count one kernel launch
 inline void count_launch(Ctx& c, int64_t k = 1) { c.launches += k; }
+
+// Product algorithm of the wide kernels (hk_set_product_algorithm).
+int product_algorithm();
+bool use_ntt(int M);
+// NTT constants for n limbs on the current device (tables built on first use).
+NttConst ntt_const(int n);
 
 // pool array `name` with at least `count` numbers of c.n limbs
 DevVec* pool_get(Ctx& c, const std::string& name, int64_t count);

@@ -1,6 +1,7 @@
 // The C ABI of libhk (declared in include/hk.h): context management, call-order
 // enforcement, host <-> device transfers and dispatch to the per-width launchers.
 #include <atomic>
+#include <mutex>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -24,6 +25,102 @@ const OpsTable* ops_for(int M) {
   HK_FOR_EACH_M(HK_CASE)
 #undef HK_CASE
   return nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// product algorithm and NTT tables
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_product_alg(HK_PRODUCT_AUTO);
+
+int product_algorithm() { return g_product_alg.load(); }
+
+bool use_ntt(int M) {
+  const int a = product_algorithm();
+  if (a == HK_PRODUCT_NTT) return 32 * M * 2 <= NTT_LMAX;
+  if (a == HK_PRODUCT_SCHOOLBOOK) return false;
+  return M >= HK_NTT_AUTO_MIN_M && 32 * M * 2 <= NTT_LMAX;
+}
+
+namespace {
+// three primes k 2^e + 1 (e >= 25) with primitive roots 31, 13, 5
+constexpr uint32_t kPrimes[NTT_Q] = {2013265921u, 1811939329u, 2113929217u};
+constexpr uint32_t kGen[NTT_Q] = {31u, 13u, 5u};
+
+uint32_t pow_mod(uint64_t b, uint64_t e, uint32_t p) {
+  uint64_t r = 1;
+  b %= p;
+  while (e) {
+    if (e & 1) r = r * b % p;
+    b = b * b % p;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+uint32_t shoup(uint32_t w, uint32_t p) { return (uint32_t)(((uint64_t)w << 32) / p); }
+uint32_t inv_mod(uint32_t a, uint32_t p) { return pow_mod(a, p - 2, p); }
+
+struct NttTables {
+  uint2* twf = nullptr;
+  uint2* twi = nullptr;
+};
+std::mutex g_ntt_mu;
+NttTables g_ntt[64];
+}  // namespace
+
+NttConst ntt_const(int n) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  NttConst nc{};
+  {
+    std::lock_guard<std::mutex> lock(g_ntt_mu);
+    NttTables& t = g_ntt[dev & 63];
+    if (!t.twf) {
+      std::vector<uint2> f((size_t)NTT_Q * NTT_LMAX / 2), iv((size_t)NTT_Q * NTT_LMAX / 2);
+      for (int q = 0; q < NTT_Q; ++q) {
+        const uint32_t p = kPrimes[q];
+        const uint32_t w = pow_mod(kGen[q], (p - 1) / NTT_LMAX, p), wi = inv_mod(w, p);
+        uint64_t a = 1, b = 1;
+        for (int k = 0; k < NTT_LMAX / 2; ++k) {
+          f[(size_t)q * NTT_LMAX / 2 + k] = make_uint2((uint32_t)a, shoup((uint32_t)a, p));
+          iv[(size_t)q * NTT_LMAX / 2 + k] = make_uint2((uint32_t)b, shoup((uint32_t)b, p));
+          a = a * w % p;
+          b = b * wi % p;
+        }
+      }
+      const size_t bytes = f.size() * sizeof(uint2);
+      if (cudaMalloc(&t.twf, bytes) == cudaSuccess && cudaMalloc(&t.twi, bytes) == cudaSuccess) {
+        cudaMemcpy(t.twf, f.data(), bytes, cudaMemcpyHostToDevice);
+        cudaMemcpy(t.twi, iv.data(), bytes, cudaMemcpyHostToDevice);
+      }
+    }
+    nc.twf = t.twf;
+    nc.twi = t.twi;
+  }
+  int L = 1, logL = 0;
+  while (L < 2 * n) {
+    L <<= 1;
+    ++logL;
+  }
+  nc.L = L;
+  nc.logL = logL;
+  for (int q = 0; q < NTT_Q; ++q) {
+    const uint32_t p = kPrimes[q];
+    nc.p[q] = p;
+    uint32_t x = p;  // Newton: x = p^{-1} mod 2^32
+    for (int it = 0; it < 5; ++it) x *= 2u - p * x;
+    nc.pinv[q] = 0u - x;
+    const uint32_t r = (uint32_t)((((uint64_t)1) << 32) % p);
+    nc.rl[q] = (uint32_t)((uint64_t)r * inv_mod((uint32_t)L, p) % p);
+    nc.rls[q] = shoup(nc.rl[q], p);
+  }
+  nc.i12 = inv_mod(kPrimes[0] % kPrimes[1], kPrimes[1]);
+  nc.i12s = shoup(nc.i12, kPrimes[1]);
+  nc.i13 = inv_mod(kPrimes[0], kPrimes[2]);
+  nc.i13s = shoup(nc.i13, kPrimes[2]);
+  nc.i23 = inv_mod(kPrimes[1], kPrimes[2]);
+  nc.i23s = shoup(nc.i23, kPrimes[2]);
+  nc.p12 = (uint64_t)kPrimes[0] * kPrimes[1];
+  return nc;
 }
 
 cudaError_t dev_alloc(DevVec& v, int64_t count, int n) {
@@ -179,6 +276,7 @@ void hk_destroy(hk_ctx* h) {
   if (c.ev_recip) cudaEventDestroy(c.ev_recip);
   if (c.aux) cudaStreamDestroy(c.aux);
   if (c.rec) cudaFree(c.rec);
+  if (c.ntt_buf) cudaFree(c.ntt_buf);
   if (c.d_err) cudaFree(c.d_err);
   delete h;
 }
@@ -357,6 +455,12 @@ hk_status hk_export(hk_ctx* h, int what, int64_t first, int64_t count, int32_t* 
     return HK_OK;
   }
   return count ? copy(0, base + first, count) : HK_OK;
+}
+
+hk_status hk_set_product_algorithm(int algorithm) {
+  if (algorithm < HK_PRODUCT_AUTO || algorithm > HK_PRODUCT_NTT) return HK_ERR_ARG;
+  g_product_alg.store(algorithm);
+  return HK_OK;
 }
 
 hk_status hk_set_profiling(hk_ctx* h, int on) {

@@ -4,6 +4,7 @@
 #pragma once
 #include "common.cuh"
 #include "mp_div.cuh"
+#include "ntt.cuh"
 
 namespace hk {
 
@@ -234,6 +235,91 @@ __global__ void __launch_bounds__(128, HK_TRAIL_MIN_BLOCKS) k_trailing(MPVec A, 
     const Result res = fused_staged<M>(sm, xc, U.sgn[c], U.exp[c], A.sgn[bpos], A.exp[bpos], A.sgn[apos],
                                        A.exp[apos], o);
     store_result<M>(A, apos, res, o);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NTT variants: products through the stored transforms (ntt.cuh)
+// ---------------------------------------------------------------------------
+// Transforms of count consecutive numbers src[first + t] into out[t * 3L ..].
+template <int M>
+__global__ void k_ntt_fwd(MPVec src, int64_t first, int count, uint32_t* __restrict__ out, NttConst nc, int scaled) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* buf = smem + wib * nc.L;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int t = blockIdx.x * (blockDim.x >> 5) + wib; t < count; t += nw)
+    warp_ntt_number<M>(src.mant + (first + t) * n, buf, out + (size_t)t * NTT_Q * nc.L, nc, scaled != 0);
+}
+
+// trunc(a - x*y) with the product from stored transforms fx (unscaled) and fy
+// (scaled); nb: this warp's 3L words of shared memory (reused for the combine).
+template <int M>
+__device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, const uint32_t* fx, bool x_zero, int sx,
+                                            int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
+                                            const uint32_t* amant, int sa_sgn, int ea, uint32_t (&out)[M]) {
+  constexpr int n = 32 * M;
+  const bool p_zero = x_zero || y_zero;
+  uint32_t lo[M], hi[M];
+  if (!p_zero) {
+    warp_mul_ntt<M>(fx, fy, nb, nc, lo, hi);
+    __syncwarp();  // every lane has read the residues before the region is reused
+  }
+  WarpSmem<M> sm(nb);
+  if (!p_zero) stage_product<M>(sm.sp, lo, hi);
+  copy_to_smem<M>(sm.sa, amant);
+  __syncwarp();
+  const bool a_zero = sm.sa[n - 1] == 0u;
+  return sub_product<M>(sm, sa_sgn, ea, a_zero, sx ^ sy, ex + ey, p_zero, out);
+}
+
+// The trailing update of step i with NTT products.  FU[c - i - 1], FB[r - i - 1]
+// hold the transforms of U[c] (unscaled) and B_i[r] (scaled) for this step.
+template <int M>
+__global__ void __launch_bounds__(128) k_trailing_ntt(MPVec A, MPVec U, const uint32_t* __restrict__ FU,
+                                                      const uint32_t* __restrict__ FB, int N, int i, int64_t t0,
+                                                      int64_t t1, NttConst nc, const int* err) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * nc.L;
+  if (*err & ERR_NOT_PD) return;
+  const int64_t m = N - 1 - i;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = t0 + (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; t < t1; t += nw) {
+    const int64_t cc = trail_col(m, t);
+    const int64_t c = i + 1 + cc;
+    const int64_t r = c + (t - trail_off(m, cc));
+    const int64_t apos = tri_pos(N, r, c);
+    const int64_t bpos = tri_pos(N, r, i);
+    const bool x_zero = U.mant[c * n + n - 1] == 0u;
+    const bool y_zero = A.mant[bpos * n + n - 1] == 0u;
+    uint32_t o[M];
+    const Result res = fused_ntt<M>(nb, nc, FU + (size_t)cc * NTT_Q * nc.L, x_zero, U.sgn[c], U.exp[c],
+                                    FB + (size_t)(r - i - 1) * NTT_Q * nc.L, y_zero, A.sgn[bpos], A.exp[bpos],
+                                    A.mant + apos * n, A.sgn[apos], A.exp[apos], o);
+    store_result<M>(A, apos, res, o);
+    __syncwarp();
+  }
+}
+
+// Elementwise trunc(a - x*y) with NTT products (FX, FY: transforms of x, y).
+template <int M>
+__global__ void k_fused_batch_ntt(MPVec a, MPVec x, MPVec y, const uint32_t* __restrict__ FX,
+                                  const uint32_t* __restrict__ FY, MPVec out, int64_t count, NttConst nc) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * nc.L;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; e < count; e += nw) {
+    uint32_t o[M];
+    const Result res = fused_ntt<M>(nb, nc, FX + (size_t)e * NTT_Q * nc.L, x.mant[e * n + n - 1] == 0u, x.sgn[e],
+                                    x.exp[e], FY + (size_t)e * NTT_Q * nc.L, y.mant[e * n + n - 1] == 0u, y.sgn[e],
+                                    y.exp[e], a.mant + e * n, a.sgn[e], a.exp[e], o);
+    store_result<M>(out, e, res, o);
     __syncwarp();
   }
 }

@@ -1,0 +1,215 @@
+// Exact limb products through a number-theoretic transform (NTT) modulo three
+// 31-bit primes, for the wide formats where schoolbook products dominate.
+//
+// The limbs of X and Y (32 bits each) are read as polynomial coefficients;
+// their product's coefficients c_t = sum_{s+u=t} x_s y_u are below
+// n 2^64 <= 2^74, far below p1 p2 p3 ~ 2^93, so the cyclic convolution of
+// length L >= 2n computed modulo each prime and recombined by the Chinese
+// remainder theorem (Garner's form) gives every c_t exactly, and the exact
+// product is sum_t c_t 2^(32 t).  Every prime has the form k 2^e + 1 with
+// e >= 25, so power-of-two lengths up to 2^25 have roots of unity.
+//
+// Layout: transforms of length L are kept in bit-reversed order (forward:
+// decimation in frequency, natural -> bit-reversed; inverse: decimation in
+// time, bit-reversed -> natural), so pointwise products need no reordering.
+// Twiddle factors w^k (k < LMAX/2, w a primitive LMAX-th root) and their
+// inverses live in a device table with Shoup companions floor(w 2^32 / p).
+#pragma once
+#include "mp_warp.cuh"
+
+namespace hk {
+
+constexpr int NTT_Q = 3;
+constexpr int NTT_LMAX = 2048;  // transform length limit: n <= 1024 limbs
+
+struct NttConst {
+  uint32_t p[NTT_Q], pinv[NTT_Q];  // primes, -p^{-1} mod 2^32 (Montgomery)
+  uint32_t rl[NTT_Q], rls[NTT_Q];  // 2^32 / L mod p and its Shoup companion
+  uint32_t i12, i12s, i13, i13s, i23, i23s;  // p1^{-1} mod p2, p1^{-1} mod p3, p2^{-1} mod p3 (+ Shoup)
+  uint64_t p12;                    // p1 p2
+  const uint2* twf;                // [q][k]: (w^k, Shoup), k < LMAX/2
+  const uint2* twi;                // [q][k]: (w^-k, Shoup)
+  int L, logL;
+};
+
+__device__ __forceinline__ uint32_t mod_add(uint32_t a, uint32_t b, uint32_t p) {
+  const uint32_t s = a + b;  // a, b < p < 2^31: no overflow
+  return s >= p ? s - p : s;
+}
+__device__ __forceinline__ uint32_t mod_sub(uint32_t a, uint32_t b, uint32_t p) { return a >= b ? a - b : a + p - b; }
+
+// x w mod p for a constant w < p with ws = floor(w 2^32 / p), any x < 2^32
+__device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t ws, uint32_t p) {
+  const uint32_t q = __umulhi(x, ws);
+  const uint32_t r = x * w - q * p;  // in [0, 2p)
+  return r >= p ? r - p : r;
+}
+
+// a b 2^-32 mod p (Montgomery), a, b < p
+__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+  const uint32_t lo = a * b, hi = __umulhi(a, b);
+  const uint32_t m = lo * pinv;
+  const uint32_t t = hi + __umulhi(m, p) + (lo != 0u ? 1u : 0u);  // (a b + m p) / 2^32 < 2p
+  return t >= p ? t - p : t;
+}
+
+// Forward transform (decimation in frequency) of buf[0..L) modulo prime q, in place.
+__device__ __forceinline__ void warp_ntt_fwd(uint32_t* buf, const NttConst& nc, int q) {
+  const uint32_t p = nc.p[q];
+  const uint2* tw = nc.twf + q * (NTT_LMAX / 2);
+  const int lane = lane_id();
+  const int half = nc.L >> 1;
+  for (int lh = nc.logL - 1; lh >= 0; --lh) {
+    const int h = 1 << lh;
+    const int tstep = (NTT_LMAX / 2) >> lh;  // w_{2h}^j = w^{j LMAX/(2h)}
+    for (int b = lane; b < half; b += 32) {
+      const int j = b & (h - 1);
+      const int i1 = ((b >> lh) << (lh + 1)) + j, i2 = i1 + h;
+      const uint32_t u = buf[i1], v = buf[i2];
+      const uint2 w = __ldg(tw + j * tstep);
+      buf[i1] = mod_add(u, v, p);
+      buf[i2] = mul_shoup(mod_sub(u, v, p), w.x, w.y, p);
+    }
+    __syncwarp();
+  }
+}
+
+// Inverse transform (decimation in time) of buf[0..L) modulo prime q, in
+// place, without the 1/L factor (it is folded into the stored transforms).
+__device__ __forceinline__ void warp_ntt_inv(uint32_t* buf, const NttConst& nc, int q) {
+  const uint32_t p = nc.p[q];
+  const uint2* tw = nc.twi + q * (NTT_LMAX / 2);
+  const int lane = lane_id();
+  const int half = nc.L >> 1;
+  for (int lh = 0; lh < nc.logL; ++lh) {
+    const int h = 1 << lh;
+    const int tstep = (NTT_LMAX / 2) >> lh;
+    for (int b = lane; b < half; b += 32) {
+      const int j = b & (h - 1);
+      const int i1 = ((b >> lh) << (lh + 1)) + j, i2 = i1 + h;
+      const uint2 w = __ldg(tw + j * tstep);
+      const uint32_t u = buf[i1], v = mul_shoup(buf[i2], w.x, w.y, p);
+      buf[i1] = mod_add(u, v, p);
+      buf[i2] = mod_sub(u, v, p);
+    }
+    __syncwarp();
+  }
+}
+
+// Transform of one n-limb mantissa (global) for all three primes into
+// out[q * L .. q * L + L).  scaled: multiply by 2^32 / L so that a Montgomery
+// product with the other operand's transform yields F(X) F(Y) / L.
+template <int M>
+__device__ __forceinline__ void warp_ntt_number(const uint32_t* __restrict__ mant, uint32_t* buf,
+                                                uint32_t* __restrict__ out, const NttConst& nc, bool scaled) {
+  constexpr int n = 32 * M;
+  const int lane = lane_id();
+  for (int q = 0; q < NTT_Q; ++q) {
+    const uint32_t p = nc.p[q];
+    for (int k = lane; k < nc.L; k += 32) {
+      uint32_t v = k < n ? mant[k] : 0u;
+      v = v >= p ? v - p : v;
+      buf[k] = v >= p ? v - p : v;  // 2^32 < 3p
+    }
+    __syncwarp();
+    warp_ntt_fwd(buf, nc, q);
+    uint32_t* o = out + (size_t)q * nc.L;
+    for (int k = lane; k < nc.L; k += 32) o[k] = scaled ? mul_shoup(buf[k], nc.rl[q], nc.rls[q], p) : buf[k];
+    __syncwarp();
+  }
+}
+
+// c_t (< 2^94) from its residues by Garner's mixed radix: c = r1 + p1 y2 + p1 p2 y3
+__device__ __forceinline__ void crt3(uint32_t r1, uint32_t r2, uint32_t r3, const NttConst& nc, uint32_t& w0,
+                                     uint32_t& w1, uint32_t& w2) {
+  const uint32_t p1 = nc.p[0], p2 = nc.p[1], p3 = nc.p[2];
+  const uint32_t r1m2 = r1 >= p2 ? r1 - p2 : r1;
+  const uint32_t y2 = mul_shoup(mod_sub(r2, r1m2, p2), nc.i12, nc.i12s, p2);
+  const uint32_t r1m3 = r1 >= p3 ? r1 - p3 : r1;
+  const uint32_t t = mul_shoup(mod_sub(r3, r1m3, p3), nc.i13, nc.i13s, p3);
+  const uint32_t y2m3 = y2 >= p3 ? y2 - p3 : y2;
+  const uint32_t y3 = mul_shoup(mod_sub(t, y2m3, p3), nc.i23, nc.i23s, p3);
+  const u128 v = (u128)nc.p12 * y3 + ((uint64_t)p1 * y2 + r1);
+  w0 = (uint32_t)v;
+  w1 = (uint32_t)(v >> 32);
+  w2 = (uint32_t)(v >> 64);
+}
+
+// Product limbs of one chunk [k0, k0 + M) from the residues res[q * L + t]
+// (natural order, c_t = 0 outside [0, 2n-1)); returns the carry out (<= 3).
+template <int M>
+__device__ __forceinline__ uint32_t crt_chunk(const uint32_t* res, int k0, const NttConst& nc, uint32_t (&out)[M]) {
+  constexpr int n = 32 * M;
+  const int L = nc.L;
+  uint32_t a1 = 0, a2 = 0, b2 = 0;  // w1(c_{k-1}), w2(c_{k-1}), w2(c_{k-2}) carried along
+  // prime the window with c_{k0-2} and c_{k0-1}
+#pragma unroll
+  for (int d = 2; d >= 1; --d) {
+    const int t = k0 - d;
+    uint32_t w0 = 0, w1 = 0, w2 = 0;
+    if (t >= 0 && t < 2 * n - 1) crt3(res[t], res[L + t], res[2 * L + t], nc, w0, w1, w2);
+    b2 = a2;
+    a1 = w1;
+    a2 = w2;
+  }
+  uint64_t carry = 0;
+#pragma unroll
+  for (int kk = 0; kk < M; ++kk) {
+    const int t = k0 + kk;
+    uint32_t w0 = 0, w1 = 0, w2 = 0;
+    if (t < 2 * n - 1) crt3(res[t], res[L + t], res[2 * L + t], nc, w0, w1, w2);
+    const uint64_t s = (uint64_t)w0 + a1 + b2 + carry;
+    out[kk] = (uint32_t)s;
+    carry = s >> 32;
+    b2 = a2;
+    a1 = w1;
+    a2 = w2;
+  }
+  // the window's leftover words of c_{k0+M-1}, c_{k0+M-2} belong to the next chunk
+  return (uint32_t)carry;
+}
+
+// Exact product P = X * Y from their stored transforms (fx: unscaled, fy:
+// scaled by 2^32/L), in the lo/hi chunk layout of warp_mul.  nb: 3L words of
+// this warp's shared memory.
+template <int M>
+__device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, const uint32_t* __restrict__ fy,
+                                             uint32_t* nb, const NttConst& nc, uint32_t (&lo)[M],
+                                             uint32_t (&hi)[M]) {
+  constexpr int n = 32 * M;
+  const int lane = lane_id();
+  const int L = nc.L;
+  for (int q = 0; q < NTT_Q; ++q) {
+    const uint32_t p = nc.p[q], pinv = nc.pinv[q];
+    const uint4* a4 = reinterpret_cast<const uint4*>(fx + (size_t)q * L);
+    const uint4* b4 = reinterpret_cast<const uint4*>(fy + (size_t)q * L);
+    uint4* o4 = reinterpret_cast<uint4*>(nb + q * L);
+    for (int k = lane; k < L / 4; k += 32) {
+      const uint4 a = a4[k], b = b4[k];
+      o4[k] = make_uint4(mont_mul(a.x, b.x, p, pinv), mont_mul(a.y, b.y, p, pinv), mont_mul(a.z, b.z, p, pinv),
+                         mont_mul(a.w, b.w, p, pinv));
+    }
+    __syncwarp();
+    warp_ntt_inv(nb + q * L, nc, q);
+  }
+  // each chunk's limbs gather c_k, c_{k-1}, c_{k-2}; the window words that
+  // spill past a chunk's top are re-derived by the next chunk (crt_chunk
+  // primes its window from c_{k0-2}, c_{k0-1}), so only carries cross lanes
+  uint32_t loc = crt_chunk<M>(nb, lane * M, nc, lo);
+  uint32_t hic = crt_chunk<M>(nb, n + lane * M, nc, hi);
+  __syncwarp();
+  for (int it = 0; it < 70; ++it) {
+    uint32_t cin_lo = __shfl_up_sync(FULL, loc, 1);
+    uint32_t cin_hi = __shfl_up_sync(FULL, hic, 1);
+    const uint32_t c31 = __shfl_sync(FULL, loc, 31);
+    if (lane == 0) {
+      cin_lo = 0;
+      cin_hi = c31;
+    }
+    if (!__any_sync(FULL, (cin_lo | cin_hi) != 0)) break;
+    loc = chunk_add_word<M>(lo, cin_lo);
+    hic = chunk_add_word<M>(hi, cin_hi);
+  }
+}
+
+}  // namespace hk

@@ -9,6 +9,18 @@
 
 namespace hk {
 
+// dynamic shared memory of `bytes` per block, and a carveout that leaves the
+// rest of the SM's 228 KB to L1 once `blocks` blocks fit
+template <typename K>
+static cudaError_t allow_smem_blocks(K kernel, size_t bytes, int blocks) {
+  const size_t total = 233472;  // 228 KB
+  int pct = (int)((blocks * (bytes + 1024) * 100 + total - 1) / total);
+  pct = pct < 1 ? 1 : (pct > 100 ? 100 : pct);
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+  if (e != cudaSuccess || bytes <= 48 * 1024) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 template <typename K>
 static cudaError_t allow_smem(K kernel, size_t bytes) {
   // prefer the largest shared-memory carveout so that shared memory does not
@@ -41,11 +53,28 @@ struct Ops {
   }
 
   static cudaError_t fused_batch(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count, cudaStream_t s) {
-    cudaError_t e = allow_smem(k_fused_batch<M>, fused_smem);
-    if (e != cudaSuccess) return e;
     if (count <= 0) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
+    if (use_ntt(M)) {
+      const NttConst nc = ntt_const(n);
+      const size_t per = (size_t)NTT_Q * nc.L;
+      uint32_t* F = nullptr;
+      cudaError_t e = cudaMallocAsync(&F, 2 * per * count * sizeof(uint32_t), s);
+      if (e != cudaSuccess) return e;
+      const size_t fsm = (size_t)WARPS * nc.L * 4, tsm = (size_t)WARPS * per * 4;
+      if ((e = allow_smem(k_ntt_fwd<M>, fsm)) != cudaSuccess) return e;
+      if ((e = allow_smem_blocks(k_fused_batch_ntt<M>, tsm, 2)) != cudaSuccess) return e;
+      const int g = (int)std::min<int64_t>((count + WARPS - 1) / WARPS, 4 * sm_count(dev));
+      k_ntt_fwd<M><<<g, 32 * WARPS, fsm, s>>>(x, 0, (int)count, F, nc, 0);
+      k_ntt_fwd<M><<<g, 32 * WARPS, fsm, s>>>(y, 0, (int)count, F + per * count, nc, 1);
+      k_fused_batch_ntt<M><<<g, 32 * WARPS, tsm, s>>>(a, x, y, F, F + per * count, out, count, nc);
+      e = cudaGetLastError();
+      cudaFreeAsync(F, s);
+      return e;
+    }
+    cudaError_t e = allow_smem(k_fused_batch<M>, fused_smem);
+    if (e != cudaSuccess) return e;
     const int64_t want = (count + WARPS - 1) / WARPS;
     const int grid = (int)std::min<int64_t>(want, resident_blocks(k_fused_batch<M>, 32 * WARPS, fused_smem, dev));
     k_fused_batch<M><<<grid, 32 * WARPS, fused_smem, s>>>(a, x, y, out, count);
@@ -87,6 +116,46 @@ struct Ops {
     if ((st = check_cuda(c, allow_smem(k_recip_pivot<M>, recip_smem), "smem attribute")) != HK_OK) return st;
     const int trail_res = resident_blocks(k_trailing<M>, 32 * WARPS, fused_smem, c.device);
     const int scale_res = resident_blocks(k_scale<M>, 32 * WARPS, div_smem, c.device);
+    // NTT products: transforms of U and B_i once per step, reused by every update
+    const bool ntt = use_ntt(M);
+    NttConst nc{};
+    size_t per = 0, ntt_smem = 0, fwd_smem = 0;
+    int ntt_res = 0, fwd_res = 0;
+    if (ntt) {
+      nc = ntt_const(n);
+      per = (size_t)NTT_Q * nc.L;
+      const size_t need = 2 * per * (size_t)N;
+      if (c.ntt_cap < need) {
+        if (c.ntt_buf) {
+          cudaStreamSynchronize(c.stream);
+          cudaFree(c.ntt_buf);
+          c.ntt_buf = nullptr;
+          c.ntt_cap = 0;
+        }
+        if ((st = check_cuda(c, cudaMalloc(&c.ntt_buf, need * 4), "allocating the transforms")) != HK_OK) return st;
+        c.ntt_cap = need;
+      }
+      ntt_smem = (size_t)WARPS * per * 4;
+      fwd_smem = (size_t)WARPS * nc.L * 4;
+      if ((st = check_cuda(c, allow_smem_blocks(k_trailing_ntt<M>, ntt_smem, 2), "smem attribute")) ||
+          (st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fwd_smem), "smem attribute")))
+        return st;
+      ntt_res = resident_blocks(k_trailing_ntt<M>, 32 * WARPS, ntt_smem, c.device);
+      fwd_res = resident_blocks(k_ntt_fwd<M>, 32 * WARPS, fwd_smem, c.device);
+    }
+    uint32_t* FU = c.ntt_buf;
+    uint32_t* FB = c.ntt_buf ? c.ntt_buf + per * (size_t)N : nullptr;
+    auto trailing = [&](int i, int64_t t0, int64_t t1) {
+      const int64_t cnt = t1 - t0;
+      if (ntt) {
+        const int g = (int)std::min<int64_t>((cnt + WARPS - 1) / WARPS, ntt_res);
+        k_trailing_ntt<M><<<g, 32 * WARPS, ntt_smem, c.stream>>>(c.A.view(), c.U.view(), FU, FB, N, i, t0, t1, nc,
+                                                                   c.d_err);
+      } else {
+        const int g = (int)std::min<int64_t>((cnt + WARPS - 1) / WARPS, trail_res);
+        k_trailing<M><<<g, 32 * WARPS, fused_smem, c.stream>>>(c.A.view(), c.U.view(), N, i, t0, t1, c.d_err);
+      }
+    };
     cudaStream_t s = c.stream;
     if (!c.aux) {
       if ((st = check_cuda(c, cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking), "aux stream")) ||
@@ -112,9 +181,15 @@ struct Ops {
       cudaStreamWaitEvent(s, c.ev_recip, 0);  // R_i is ready
       const int gs = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, scale_res);
       k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(c.A.view(), c.U.view(), N, i, c.rec, c.rec_meta, c.d_err);
+      if (ntt) {  // transforms of U[i+1..N) and of B_i = A[i+1..N][i]
+        const int g = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, fwd_res);
+        k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.U.view(), i + 1, (int)rows, FU, nc, 0);
+        k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FB, nc, 1);
+        count_launch(c, 2);
+      }
       // look-ahead: update d_{i+1} = A[i+1][i+1] first (entry t = 0 of the trailing triangle) ...
       const size_t e0 = c.prof ? prof_mark(c) : 0;
-      k_trailing<M><<<1, 32 * WARPS, fused_smem, s>>>(c.A.view(), c.U.view(), N, i, 0, 1, c.d_err);
+      trailing(i, 0, 1);
       if (c.prof) {
         c.trail_ev.push_back({e0, prof_mark(c)});
         c.trail_macs += (double)n * n;
@@ -126,9 +201,8 @@ struct Ops {
       cudaEventRecord(c.ev_recip, c.aux);
       // ... while the main stream updates the rest of the trailing triangle
       if (T > 1) {
-        const int gt = (int)std::min<int64_t>((T - 1 + WARPS - 1) / WARPS, trail_res);
         const size_t e1 = c.prof ? prof_mark(c) : 0;
-        k_trailing<M><<<gt, 32 * WARPS, fused_smem, s>>>(c.A.view(), c.U.view(), N, i, 1, T, c.d_err);
+        trailing(i, 1, T);
         if (c.prof) {
           c.trail_ev.push_back({e1, prof_mark(c)});
           c.trail_macs += (double)(T - 1) * n * n;  // n^2 limb products per fused operation

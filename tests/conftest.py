@@ -28,3 +28,13 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture
+def product_algorithm(request):
+    """Run a GPU test with the given exact-product algorithm, restoring AUTO after."""
+    import paper_1810_01478_gb300 as hk
+    hk.load()
+    hk.hk_set_product_algorithm(request.param)
+    yield request.param
+    hk.hk_set_product_algorithm(hk.HK_PRODUCT_AUTO)

@@ -4,7 +4,8 @@ hk_fused_batch computes trunc(a - x*y) and hk_div_batch trunc(a/d) on the
 device; the oracle's mpfloat.fused / mpfloat.div are the reference.  Operands
 come from tests/inputs.fused_operands: random and structured mantissas,
 near-total cancellation, exponent gaps beyond the combine frame (sticky
-cases) and zeros, at widths of 1, 4 and 24 limbs per lane.
+cases) and zeros, at widths of 1, 4 and 24 limbs per lane, with both exact
+product algorithms (schoolbook limb products and the three-prime NTT).
 """
 import random
 
@@ -24,8 +25,12 @@ def first_mismatch(got, want, ops):
     return None
 
 
+SCHOOLBOOK, NTT = 1, 2
+
+
+@pytest.mark.parametrize("product_algorithm", [SCHOOLBOOK, NTT], indirect=True)
 @pytest.mark.parametrize("M", [1, 2, 4, 7, 24])
-def test_fused_batch_bit_exact(M):
+def test_fused_batch_bit_exact(M, product_algorithm):
     import torch
     import paper_1810_01478_gb300 as hk
     n = 32 * M

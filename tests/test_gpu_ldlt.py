@@ -48,8 +48,9 @@ def test_moments_bit_exact(beta, N, bits):
     assert got == OM.moments(Fraction(*beta), N, n)
 
 
-@pytest.mark.parametrize("N,bits", [(48, 4096), (1, 4096), (2, 1024), (33, 1024), (20, 24576)])
-def test_ldlt_beta_half_bit_exact(N, bits):
+@pytest.mark.parametrize("product_algorithm", [1, 2], indirect=True)
+@pytest.mark.parametrize("N,bits", [(48, 4096), (1, 4096), (2, 1024), (33, 1024), (20, 24576), (40, 8192)])
+def test_ldlt_beta_half_bit_exact(N, bits, product_algorithm):
     import paper_1810_01478_gb300 as hk
     n = bits // 32
     mu = OM.moments(Fraction(1, 2), N, n)
@@ -93,3 +94,22 @@ def test_not_positive_definite_is_reported():
         assert ei.value.status == hk.HK_ERR_NOT_PD
     finally:
         h.close()
+
+
+def test_schoolbook_and_ntt_factors_identical():
+    """The two exact-product algorithms give the same factor bit for bit
+    (N = 160 at 12288 bits; digests of the whole packed factor)."""
+    import paper_1810_01478_gb300 as hk
+    from tests.digest import factor_digest
+    hk.load()
+    digests = []
+    try:
+        for alg in (hk.HK_PRODUCT_SCHOOLBOOK, hk.HK_PRODUCT_NTT):
+            hk.hk_set_product_algorithm(alg)
+            with hk.Hankel(0) as h:
+                h.moments(1, 2, 160, 12288)
+                h.ldlt()
+                digests.append(factor_digest(h, hk, 160))
+    finally:
+        hk.hk_set_product_algorithm(hk.HK_PRODUCT_AUTO)
+    assert digests[0] == digests[1]
