@@ -42,9 +42,10 @@ bool use_ntt(int M) {
 }
 
 namespace {
-// three primes k 2^e + 1 (e >= 25) with primitive roots 31, 13, 5
-constexpr uint32_t kPrimes[NTT_Q] = {2013265921u, 1811939329u, 2113929217u};
-constexpr uint32_t kGen[NTT_Q] = {31u, 13u, 5u};
+// three primes k 2^e + 1 below 2^30 (e = 20, 21, 23; p1 > p2 > p3, p1 < 2 p3)
+// with primitive roots 7, 5, 3
+constexpr uint32_t kPrimes[NTT_Q] = {1053818881u, 1012924417u, 998244353u};
+constexpr uint32_t kGen[NTT_Q] = {7u, 5u, 3u};
 
 uint32_t pow_mod(uint64_t b, uint64_t e, uint32_t p) {
   uint64_t r = 1;

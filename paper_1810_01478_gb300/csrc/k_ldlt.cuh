@@ -248,14 +248,14 @@ __global__ void k_ntt_fwd(MPVec src, int64_t first, int count, uint32_t* __restr
   constexpr int n = 32 * M;
   extern __shared__ uint32_t smem[];
   const int wib = threadIdx.x >> 5;
-  uint32_t* buf = smem + wib * nc.L;
+  uint32_t* buf = smem + wib * ntt_stride(nc.L);
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int t = blockIdx.x * (blockDim.x >> 5) + wib; t < count; t += nw)
     warp_ntt_number<M>(src.mant + (first + t) * n, buf, out + (size_t)t * NTT_Q * nc.L, nc, scaled != 0);
 }
 
 // trunc(a - x*y) with the product from stored transforms fx (unscaled) and fy
-// (scaled); nb: this warp's 3L words of shared memory (reused for the combine).
+// (scaled); nb: this warp's 3 ntt_stride(L) words of shared memory (reused for the combine).
 template <int M>
 __device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, const uint32_t* fx, bool x_zero, int sx,
                                             int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(128) k_trailing_ntt(MPVec A, MPVec U, const ui
   constexpr int n = 32 * M;
   extern __shared__ uint32_t smem[];
   const int wib = threadIdx.x >> 5;
-  uint32_t* nb = smem + (size_t)wib * NTT_Q * nc.L;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * ntt_stride(nc.L);
   if (*err & ERR_NOT_PD) return;
   const int64_t m = N - 1 - i;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -312,7 +312,7 @@ __global__ void k_fused_batch_ntt(MPVec a, MPVec x, MPVec y, const uint32_t* __r
   constexpr int n = 32 * M;
   extern __shared__ uint32_t smem[];
   const int wib = threadIdx.x >> 5;
-  uint32_t* nb = smem + (size_t)wib * NTT_Q * nc.L;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * ntt_stride(nc.L);
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t e = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; e < count; e += nw) {
     uint32_t o[M];

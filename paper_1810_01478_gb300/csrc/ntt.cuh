@@ -1,19 +1,25 @@
 // Exact limb products through a number-theoretic transform (NTT) modulo three
-// 31-bit primes, for the wide formats where schoolbook products dominate.
+// 30-bit primes, for the wide formats where schoolbook products dominate.
 //
 // The limbs of X and Y (32 bits each) are read as polynomial coefficients;
 // their product's coefficients c_t = sum_{s+u=t} x_s y_u are below
-// n 2^64 <= 2^74, far below p1 p2 p3 ~ 2^93, so the cyclic convolution of
+// n 2^64 <= 2^74, far below p1 p2 p3 ~ 2^90, so the cyclic convolution of
 // length L >= 2n computed modulo each prime and recombined by the Chinese
 // remainder theorem (Garner's form) gives every c_t exactly, and the exact
-// product is sum_t c_t 2^(32 t).  Every prime has the form k 2^e + 1 with
-// e >= 25, so power-of-two lengths up to 2^25 have roots of unity.
+// product is sum_t c_t 2^(32 t).  Every prime is below 2^30 and has the form
+// k 2^e + 1 with e >= 20, so power-of-two lengths up to 2^20 have roots of
+// unity.
 //
 // Layout: transforms of length L are kept in bit-reversed order (forward:
 // decimation in frequency, natural -> bit-reversed; inverse: decimation in
 // time, bit-reversed -> natural), so pointwise products need no reordering.
 // Twiddle factors w^k (k < LMAX/2, w a primitive LMAX-th root) and their
 // inverses live in a device table with Shoup companions floor(w 2^32 / p).
+//
+// Speed: butterflies are lazy (values kept in [0, 2p) or [0, 4p), which fit
+// 32 bits because p < 2^30; reductions happen once at the ends), three stages
+// run per pass on eight elements held in registers, and shared memory is
+// padded by one word per 32 so that short-stride passes avoid bank conflicts.
 #pragma once
 #include "mp_warp.cuh"
 
@@ -33,93 +39,168 @@ struct NttConst {
 };
 
 __device__ __forceinline__ uint32_t mod_add(uint32_t a, uint32_t b, uint32_t p) {
-  const uint32_t s = a + b;  // a, b < p < 2^31: no overflow
+  const uint32_t s = a + b;  // a, b < p < 2^30: no overflow
   return s >= p ? s - p : s;
 }
 __device__ __forceinline__ uint32_t mod_sub(uint32_t a, uint32_t b, uint32_t p) { return a >= b ? a - b : a + p - b; }
 
-// x w mod p for a constant w < p with ws = floor(w 2^32 / p), any x < 2^32
+// x w mod p, lazily in [0, 2p), for a constant w < p with ws = floor(w 2^32 / p), any x < 2^32
+__device__ __forceinline__ uint32_t mul_shoup_lazy(uint32_t x, uint32_t w, uint32_t ws, uint32_t p) {
+  return x * w - __umulhi(x, ws) * p;
+}
 __device__ __forceinline__ uint32_t mul_shoup(uint32_t x, uint32_t w, uint32_t ws, uint32_t p) {
-  const uint32_t q = __umulhi(x, ws);
-  const uint32_t r = x * w - q * p;  // in [0, 2p)
+  const uint32_t r = mul_shoup_lazy(x, w, ws, p);
   return r >= p ? r - p : r;
 }
 
-// a b 2^-32 mod p (Montgomery), a, b < p
-__device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
+// a b 2^-32 mod p (Montgomery), lazily in [0, 2p); a, b < p
+__device__ __forceinline__ uint32_t mont_mul_lazy(uint32_t a, uint32_t b, uint32_t p, uint32_t pinv) {
   const uint32_t lo = a * b, hi = __umulhi(a, b);
   const uint32_t m = lo * pinv;
-  const uint32_t t = hi + __umulhi(m, p) + (lo != 0u ? 1u : 0u);  // (a b + m p) / 2^32 < 2p
-  return t >= p ? t - p : t;
+  return hi + __umulhi(m, p) + (lo != 0u ? 1u : 0u);  // (a b + m p) / 2^32
 }
 
-// Forward transform (decimation in frequency) of buf[0..L) modulo prime q, in place.
-__device__ __forceinline__ void warp_ntt_fwd(uint32_t* buf, const NttConst& nc, int q) {
-  const uint32_t p = nc.p[q];
-  const uint2* tw = nc.twf + q * (NTT_LMAX / 2);
-  const int lane = lane_id();
-  const int half = nc.L >> 1;
-  for (int lh = nc.logL - 1; lh >= 0; --lh) {
-    const int h = 1 << lh;
-    const int tstep = (NTT_LMAX / 2) >> lh;  // w_{2h}^j = w^{j LMAX/(2h)}
-    for (int b = lane; b < half; b += 32) {
-      const int j = b & (h - 1);
-      const int i1 = ((b >> lh) << (lh + 1)) + j, i2 = i1 + h;
-      const uint32_t u = buf[i1], v = buf[i2];
-      const uint2 w = __ldg(tw + j * tstep);
-      buf[i1] = mod_add(u, v, p);
-      buf[i2] = mul_shoup(mod_sub(u, v, p), w.x, w.y, p);
+// a[q] for a runtime q without spilling the constant struct to local memory
+__device__ __forceinline__ uint32_t sel3(const uint32_t (&a)[NTT_Q], int q) {
+  return q == 0 ? a[0] : (q == 1 ? a[1] : a[2]);
+}
+
+// [0, 4p) -> [0, p)
+__device__ __forceinline__ uint32_t reduce4(uint32_t x, uint32_t p) {
+  x = x >= 2 * p ? x - 2 * p : x;
+  return x >= p ? x - p : x;
+}
+
+// padded shared-memory index of transform element i (one word of padding per 32)
+__device__ __forceinline__ int npad(int i) { return i + (i >> 5); }
+__host__ __device__ constexpr int ntt_stride(int L) { return L + L / 32; }
+
+// One pass of S stages on groups of R = 2^S elements i = hi 2^(s+S) + m 2^s + lo.
+// forward (decimation in frequency, stages s+S-1 .. s): [0, 2p) -> [0, 2p)
+template <int S>
+__device__ __forceinline__ void dif_pass(uint32_t* buf, int L, int s, const uint2* __restrict__ tw, uint32_t p) {
+  constexpr int R = 1 << S;
+  const int groups = L >> S;
+  const uint32_t p2 = 2 * p;
+  for (int g = lane_id(); g < groups; g += 32) {
+    const int lo = g & ((1 << s) - 1);
+    const int base = ((g >> s) << (s + S)) + lo;
+    uint32_t x[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) x[m] = buf[npad(base + (m << s))];
+#pragma unroll
+    for (int t = S - 1; t >= 0; --t) {
+      const int tstep = (NTT_LMAX / 2) >> (s + t);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (m & (1 << t)) continue;
+        const int j = ((m & ((1 << t) - 1)) << s) + lo;
+        const uint2 w = __ldg(tw + j * tstep);
+        const uint32_t u = x[m], v = x[m + (1 << t)];
+        const uint32_t sm = u + v;
+        x[m] = sm >= p2 ? sm - p2 : sm;
+        x[m + (1 << t)] = mul_shoup_lazy(u - v + p2, w.x, w.y, p);
+      }
     }
-    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < R; ++m) buf[npad(base + (m << s))] = x[m];
   }
 }
 
-// Inverse transform (decimation in time) of buf[0..L) modulo prime q, in
-// place, without the 1/L factor (it is folded into the stored transforms).
-__device__ __forceinline__ void warp_ntt_inv(uint32_t* buf, const NttConst& nc, int q) {
-  const uint32_t p = nc.p[q];
-  const uint2* tw = nc.twi + q * (NTT_LMAX / 2);
-  const int lane = lane_id();
-  const int half = nc.L >> 1;
-  for (int lh = 0; lh < nc.logL; ++lh) {
-    const int h = 1 << lh;
-    const int tstep = (NTT_LMAX / 2) >> lh;
-    for (int b = lane; b < half; b += 32) {
-      const int j = b & (h - 1);
-      const int i1 = ((b >> lh) << (lh + 1)) + j, i2 = i1 + h;
-      const uint2 w = __ldg(tw + j * tstep);
-      const uint32_t u = buf[i1], v = mul_shoup(buf[i2], w.x, w.y, p);
-      buf[i1] = mod_add(u, v, p);
-      buf[i2] = mod_sub(u, v, p);
+// inverse (decimation in time, stages s .. s+S-1): [0, 4p) -> [0, 4p)
+template <int S>
+__device__ __forceinline__ void dit_pass(uint32_t* buf, int L, int s, const uint2* __restrict__ tw, uint32_t p) {
+  constexpr int R = 1 << S;
+  const int groups = L >> S;
+  const uint32_t p2 = 2 * p;
+  for (int g = lane_id(); g < groups; g += 32) {
+    const int lo = g & ((1 << s) - 1);
+    const int base = ((g >> s) << (s + S)) + lo;
+    uint32_t x[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) x[m] = buf[npad(base + (m << s))];
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      const int tstep = (NTT_LMAX / 2) >> (s + t);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (m & (1 << t)) continue;
+        const int j = ((m & ((1 << t) - 1)) << s) + lo;
+        const uint2 w = __ldg(tw + j * tstep);
+        uint32_t X = x[m];
+        X = X >= p2 ? X - p2 : X;
+        const uint32_t T = mul_shoup_lazy(x[m + (1 << t)], w.x, w.y, p);
+        x[m] = X + T;
+        x[m + (1 << t)] = X - T + p2;
+      }
     }
+#pragma unroll
+    for (int m = 0; m < R; ++m) buf[npad(base + (m << s))] = x[m];
+  }
+}
+
+// Forward transform of the padded buf modulo prime q, in place ([0, 2p) in and out).
+__device__ __forceinline__ void warp_ntt_fwd(uint32_t* buf, const NttConst& nc, int q) {
+  const uint32_t p = sel3(nc.p, q);
+  const uint2* tw = nc.twf + q * (NTT_LMAX / 2);
+  int top = nc.logL;
+  while (top > 0) {
+    const int S = top >= 3 ? 3 : top;
+    const int s = top - S;
+    if (S == 3) dif_pass<3>(buf, nc.L, s, tw, p);
+    else if (S == 2) dif_pass<2>(buf, nc.L, s, tw, p);
+    else dif_pass<1>(buf, nc.L, s, tw, p);
     __syncwarp();
+    top = s;
+  }
+}
+
+// Inverse transform of the padded buf modulo prime q, in place, without the
+// 1/L factor (folded into the stored transforms); [0, 4p) in and out.
+__device__ __forceinline__ void warp_ntt_inv(uint32_t* buf, const NttConst& nc, int q) {
+  const uint32_t p = sel3(nc.p, q);
+  const uint2* tw = nc.twi + q * (NTT_LMAX / 2);
+  for (int s = 0; s < nc.logL;) {
+    const int S = nc.logL - s >= 3 ? 3 : nc.logL - s;
+    if (S == 3) dit_pass<3>(buf, nc.L, s, tw, p);
+    else if (S == 2) dit_pass<2>(buf, nc.L, s, tw, p);
+    else dit_pass<1>(buf, nc.L, s, tw, p);
+    __syncwarp();
+    s += S;
   }
 }
 
 // Transform of one n-limb mantissa (global) for all three primes into
-// out[q * L .. q * L + L).  scaled: multiply by 2^32 / L so that a Montgomery
-// product with the other operand's transform yields F(X) F(Y) / L.
+// out[q * L .. q * L + L) (reduced, unpadded).  buf: ntt_stride(L) words of
+// shared memory.  scaled: multiply by 2^32 / L so that a Montgomery product
+// with the other operand's transform yields F(X) F(Y) / L.
 template <int M>
 __device__ __forceinline__ void warp_ntt_number(const uint32_t* __restrict__ mant, uint32_t* buf,
                                                 uint32_t* __restrict__ out, const NttConst& nc, bool scaled) {
   constexpr int n = 32 * M;
   const int lane = lane_id();
+#pragma unroll 1
   for (int q = 0; q < NTT_Q; ++q) {
-    const uint32_t p = nc.p[q];
+    const uint32_t p = sel3(nc.p, q), rl = sel3(nc.rl, q), rls = sel3(nc.rls, q);
     for (int k = lane; k < nc.L; k += 32) {
       uint32_t v = k < n ? mant[k] : 0u;
-      v = v >= p ? v - p : v;
-      buf[k] = v >= p ? v - p : v;  // 2^32 < 3p
+      v = v >= 2 * p ? v - 2 * p : v;  // 2^32 < 4p: now in [0, 2p)
+      buf[npad(k)] = v >= 2 * p ? v - 2 * p : v;
     }
     __syncwarp();
     warp_ntt_fwd(buf, nc, q);
     uint32_t* o = out + (size_t)q * nc.L;
-    for (int k = lane; k < nc.L; k += 32) o[k] = scaled ? mul_shoup(buf[k], nc.rl[q], nc.rls[q], p) : buf[k];
+    for (int k = lane; k < nc.L; k += 32) {
+      uint32_t v = buf[npad(k)];
+      v = v >= p ? v - p : v;
+      o[k] = scaled ? mul_shoup(v, rl, rls, p) : v;
+    }
     __syncwarp();
   }
 }
 
-// c_t (< 2^94) from its residues by Garner's mixed radix: c = r1 + p1 y2 + p1 p2 y3
+// c_t (< 2^90) from its residues (each < p) by Garner's mixed radix:
+// c = r1 + p1 y2 + p1 p2 y3 (p1 > p2 > p3 and p1 < 2 p3)
 __device__ __forceinline__ void crt3(uint32_t r1, uint32_t r2, uint32_t r3, const NttConst& nc, uint32_t& w0,
                                      uint32_t& w1, uint32_t& w2) {
   const uint32_t p1 = nc.p[0], p2 = nc.p[1], p3 = nc.p[2];
@@ -140,14 +221,17 @@ __device__ __forceinline__ void crt3(uint32_t r1, uint32_t r2, uint32_t r3, cons
 template <int M>
 __device__ __forceinline__ uint32_t crt_chunk(const uint32_t* res, int k0, const NttConst& nc, uint32_t (&out)[M]) {
   constexpr int n = 32 * M;
-  const int L = nc.L;
+  const int st = ntt_stride(nc.L);
+  const uint32_t p1 = nc.p[0], p2 = nc.p[1], p3 = nc.p[2];
   uint32_t a1 = 0, a2 = 0, b2 = 0;  // w1(c_{k-1}), w2(c_{k-1}), w2(c_{k-2}) carried along
   // prime the window with c_{k0-2} and c_{k0-1}
 #pragma unroll
   for (int d = 2; d >= 1; --d) {
     const int t = k0 - d;
     uint32_t w0 = 0, w1 = 0, w2 = 0;
-    if (t >= 0 && t < 2 * n - 1) crt3(res[t], res[L + t], res[2 * L + t], nc, w0, w1, w2);
+    if (t >= 0 && t < 2 * n - 1)
+      crt3(reduce4(res[npad(t)], p1), reduce4(res[st + npad(t)], p2), reduce4(res[2 * st + npad(t)], p3), nc, w0, w1,
+           w2);
     b2 = a2;
     a1 = w1;
     a2 = w2;
@@ -157,7 +241,9 @@ __device__ __forceinline__ uint32_t crt_chunk(const uint32_t* res, int k0, const
   for (int kk = 0; kk < M; ++kk) {
     const int t = k0 + kk;
     uint32_t w0 = 0, w1 = 0, w2 = 0;
-    if (t < 2 * n - 1) crt3(res[t], res[L + t], res[2 * L + t], nc, w0, w1, w2);
+    if (t < 2 * n - 1)
+      crt3(reduce4(res[npad(t)], p1), reduce4(res[st + npad(t)], p2), reduce4(res[2 * st + npad(t)], p3), nc, w0, w1,
+           w2);
     const uint64_t s = (uint64_t)w0 + a1 + b2 + carry;
     out[kk] = (uint32_t)s;
     carry = s >> 32;
@@ -170,27 +256,31 @@ __device__ __forceinline__ uint32_t crt_chunk(const uint32_t* res, int k0, const
 }
 
 // Exact product P = X * Y from their stored transforms (fx: unscaled, fy:
-// scaled by 2^32/L), in the lo/hi chunk layout of warp_mul.  nb: 3L words of
-// this warp's shared memory.
+// scaled by 2^32/L), in the lo/hi chunk layout of warp_mul.  nb:
+// 3 ntt_stride(L) words of this warp's shared memory.
 template <int M>
 __device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, const uint32_t* __restrict__ fy,
                                              uint32_t* nb, const NttConst& nc, uint32_t (&lo)[M],
                                              uint32_t (&hi)[M]) {
   constexpr int n = 32 * M;
   const int lane = lane_id();
-  const int L = nc.L;
+  const int L = nc.L, st = ntt_stride(L);
+#pragma unroll 1
   for (int q = 0; q < NTT_Q; ++q) {
-    const uint32_t p = nc.p[q], pinv = nc.pinv[q];
+    const uint32_t p = sel3(nc.p, q), pinv = sel3(nc.pinv, q);
     const uint4* a4 = reinterpret_cast<const uint4*>(fx + (size_t)q * L);
     const uint4* b4 = reinterpret_cast<const uint4*>(fy + (size_t)q * L);
-    uint4* o4 = reinterpret_cast<uint4*>(nb + q * L);
+    uint32_t* o = nb + q * st;
     for (int k = lane; k < L / 4; k += 32) {
       const uint4 a = a4[k], b = b4[k];
-      o4[k] = make_uint4(mont_mul(a.x, b.x, p, pinv), mont_mul(a.y, b.y, p, pinv), mont_mul(a.z, b.z, p, pinv),
-                         mont_mul(a.w, b.w, p, pinv));
+      const int i = npad(4 * k);  // the four words share one padding block
+      o[i] = mont_mul_lazy(a.x, b.x, p, pinv);
+      o[i + 1] = mont_mul_lazy(a.y, b.y, p, pinv);
+      o[i + 2] = mont_mul_lazy(a.z, b.z, p, pinv);
+      o[i + 3] = mont_mul_lazy(a.w, b.w, p, pinv);
     }
     __syncwarp();
-    warp_ntt_inv(nb + q * L, nc, q);
+    warp_ntt_inv(o, nc, q);
   }
   // each chunk's limbs gather c_k, c_{k-1}, c_{k-2}; the window words that
   // spill past a chunk's top are re-derived by the next chunk (crt_chunk

@@ -62,7 +62,7 @@ struct Ops {
       uint32_t* F = nullptr;
       cudaError_t e = cudaMallocAsync(&F, 2 * per * count * sizeof(uint32_t), s);
       if (e != cudaSuccess) return e;
-      const size_t fsm = (size_t)WARPS * nc.L * 4, tsm = (size_t)WARPS * per * 4;
+      const size_t fsm = (size_t)WARPS * ntt_stride(nc.L) * 4, tsm = (size_t)WARPS * NTT_Q * ntt_stride(nc.L) * 4;
       if ((e = allow_smem(k_ntt_fwd<M>, fsm)) != cudaSuccess) return e;
       if ((e = allow_smem_blocks(k_fused_batch_ntt<M>, tsm, 2)) != cudaSuccess) return e;
       const int g = (int)std::min<int64_t>((count + WARPS - 1) / WARPS, 4 * sm_count(dev));
@@ -135,8 +135,8 @@ struct Ops {
         if ((st = check_cuda(c, cudaMalloc(&c.ntt_buf, need * 4), "allocating the transforms")) != HK_OK) return st;
         c.ntt_cap = need;
       }
-      ntt_smem = (size_t)WARPS * per * 4;
-      fwd_smem = (size_t)WARPS * nc.L * 4;
+      ntt_smem = (size_t)WARPS * NTT_Q * ntt_stride(nc.L) * 4;
+      fwd_smem = (size_t)WARPS * ntt_stride(nc.L) * 4;
       if ((st = check_cuda(c, allow_smem_blocks(k_trailing_ntt<M>, ntt_smem, 2), "smem attribute")) ||
           (st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fwd_smem), "smem attribute")))
         return st;
