@@ -188,6 +188,42 @@ __global__ void __launch_bounds__(128) k_alg4_step(MPVec A, MPVec X, int N, int 
   }
 }
 
+// Algorithm 4 step i with NTT products: FL[j - i - 1] = transform of L[j][i]
+// (unscaled), FXr[c] = transform of X[i][c] (scaled).
+template <int M>
+__global__ void __launch_bounds__(128) k_alg4_ntt(MPVec A, MPVec X, const uint32_t* __restrict__ FL,
+                                                  const uint32_t* __restrict__ FXr, int N, int k, int i, NttConst nc) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * ntt_stride(nc.L);
+  const int cols = min(k, i);
+  const int per_row = cols + (i < k ? 1 : 0);
+  const int64_t total = (int64_t)(N - 1 - i) * per_row;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t t = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; t < total; t += nw) {
+    const int64_t j = i + 1 + t / per_row;
+    const int c = (int)(t % per_row);
+    const int64_t fpos = tri_pos(N, j, i);
+    if (c == cols) {  // X[j][i] = -L[j][i]
+      uint32_t v[M];
+      load_chunk<M>(A.mant + fpos * n, v);
+      const bool zero = __shfl_sync(FULL, v[M - 1], 31) == 0u;
+      Result r{zero ? 0 : (A.sgn[fpos] ^ 1), A.exp[fpos], zero};
+      store_result<M>(X, j * k + i, r, v);
+      continue;
+    }
+    const int64_t apos = j * k + c, ypos = (int64_t)i * k + c;
+    uint32_t o[M];
+    const Result r = fused_ntt<M>(nb, nc, FL + (size_t)(j - i - 1) * NTT_Q * nc.L, A.mant[fpos * n + n - 1] == 0u,
+                                  A.sgn[fpos], A.exp[fpos], FXr + (size_t)c * NTT_Q * nc.L,
+                                  X.mant[ypos * n + n - 1] == 0u, X.sgn[ypos], X.exp[ypos], X.mant + apos * n,
+                                  X.sgn[apos], X.exp[apos], o);
+    store_result<M>(X, apos, r, o);
+    __syncwarp();
+  }
+}
+
 // X[r][c] = 1 if r == c (c < k), else 0, for the rows r <= c that Algorithm 4 never writes.
 template <int M>
 __global__ void k_x_init(MPVec X, int N, int k) {

@@ -27,11 +27,17 @@ static double to_double(int32_t s, int32_t e, const uint32_t* m, int n) {
   return s ? -r : r;
 }
 
+static int ntt_const_L(int n) {
+  int L = 1;
+  while (L < 2 * n) L <<= 1;
+  return L;
+}
+
 template <int M>
 struct Tail {
   static constexpr int n = 32 * M;
   static constexpr int W = Ops<M>::WARPS;
-  static constexpr int SEG = 16;  // chain length of one partial sum
+  static constexpr int SEG = 8;  // chain length of one partial sum (latency of a dot product ~ SEG + its reduction)
 
   static hk_status chains(Ctx& c, const std::vector<ChainTask>& t, MPVec X, MPVec Y, MPVec INIT, MPVec OUT) {
     if (t.empty()) return HK_OK;
@@ -103,7 +109,7 @@ struct Tail {
     if (d.empty()) return HK_OK;
     int maxlen = 0;
     for (const Dot& e : d) maxlen = std::max(maxlen, e.len);
-    if (maxlen <= 2 * SEG) {
+    if (maxlen <= SEG) {
       std::vector<ChainTask> t;
       t.reserve(d.size());
       for (const Dot& e : d)
@@ -155,17 +161,49 @@ struct Tail {
       k_x_init<M><<<grid, 256, 0, c.stream>>>(c.X.view(), N, k);
       count_launch(c);
     }
-    const size_t smem = Ops<M>::fused_smem;
-    if ((st = check_cuda(c, allow_smem(k_alg4_step<M>, smem), "smem attribute")) != HK_OK) return st;
-    const int res = Ops<M>::resident_blocks(k_alg4_step<M>, 32 * W, smem, c.device);
-    // Algorithm 4: N-1 steps in increasing pivot order
-    for (int i = 0; i < N - 1; ++i) {
-      const int64_t per_row = std::min(k, i) + (i < k ? 1 : 0);
-      const int64_t total = (int64_t)(N - 1 - i) * per_row;
-      if (total == 0) continue;
-      const int grid = (int)std::min<int64_t>((total + W - 1) / W, res);
-      k_alg4_step<M><<<grid, 32 * W, smem, c.stream>>>(c.A.view(), c.X.view(), N, k, i);
-      count_launch(c);
+    const bool ntt = use_ntt(M) && c.ntt_buf && c.ntt_cap >= 2 * (size_t)NTT_Q * ntt_const_L(n) * N;
+    if (ntt) {
+      // Algorithm 4 with NTT products: per step, the transforms of the pivot
+      // column L[i+1..N)[i] (unscaled) and of the finished row X[i][0..cols) (scaled)
+      const NttConst nc = ntt_const(n);
+      const size_t per = (size_t)NTT_Q * nc.L;
+      uint32_t* FL = c.ntt_buf;
+      uint32_t* FXr = c.ntt_buf + per * N;
+      const size_t tsm = (size_t)W * NTT_Q * ntt_stride(nc.L) * 4, fsm = (size_t)W * ntt_stride(nc.L) * 4;
+      if ((st = check_cuda(c, allow_smem_blocks(k_alg4_ntt<M>, tsm, 2), "smem attribute")) ||
+          (st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fsm), "smem attribute")))
+        return st;
+      const int res = Ops<M>::resident_blocks(k_alg4_ntt<M>, 32 * W, tsm, c.device);
+      const int fres = Ops<M>::resident_blocks(k_ntt_fwd<M>, 32 * W, fsm, c.device);
+      for (int i = 0; i < N - 1; ++i) {
+        const int cols = std::min(k, i);
+        const int64_t per_row = cols + (i < k ? 1 : 0);
+        const int64_t rows = N - 1 - i;
+        const int64_t total = rows * per_row;
+        if (cols > 0) {
+          const int g1 = (int)std::min<int64_t>((rows + W - 1) / W, fres);
+          k_ntt_fwd<M><<<g1, 32 * W, fsm, c.stream>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FL, nc, 0);
+          const int g2 = (int)std::min<int64_t>((cols + W - 1) / W, fres);
+          k_ntt_fwd<M><<<g2, 32 * W, fsm, c.stream>>>(c.X.view(), (int64_t)i * k, cols, FXr, nc, 1);
+          count_launch(c, 2);
+        }
+        const int grid = (int)std::min<int64_t>((total + W - 1) / W, res);
+        k_alg4_ntt<M><<<grid, 32 * W, tsm, c.stream>>>(c.A.view(), c.X.view(), FL, FXr, N, k, i, nc);
+        count_launch(c);
+      }
+    } else {
+      const size_t smem = Ops<M>::fused_smem;
+      if ((st = check_cuda(c, allow_smem(k_alg4_step<M>, smem), "smem attribute")) != HK_OK) return st;
+      const int res = Ops<M>::resident_blocks(k_alg4_step<M>, 32 * W, smem, c.device);
+      // Algorithm 4: N-1 steps in increasing pivot order
+      for (int i = 0; i < N - 1; ++i) {
+        const int64_t per_row = std::min(k, i) + (i < k ? 1 : 0);
+        const int64_t total = (int64_t)(N - 1 - i) * per_row;
+        if (total == 0) continue;
+        const int grid = (int)std::min<int64_t>((total + W - 1) / W, res);
+        k_alg4_step<M><<<grid, 32 * W, smem, c.stream>>>(c.A.view(), c.X.view(), N, k, i);
+        count_launch(c);
+      }
     }
     if ((st = check_cuda(c, cudaGetLastError(), "Algorithm 4")) != HK_OK) return st;
     // reciprocals of the pivots (kept for the gradient), then Y[l][b] = X[l][b] / D_l
