@@ -158,7 +158,7 @@ HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 #define HK_PRODUCT_AUTO 0
 #define HK_PRODUCT_SCHOOLBOOK 1
 #define HK_PRODUCT_NTT 2
-#define HK_NTT_AUTO_MIN_M 12
+#define HK_NTT_AUTO_MIN_M 8
 HK_API hk_status hk_set_product_algorithm(int algorithm);
 
 /* Elementwise primitives on caller-owned DEVICE arrays of `count` numbers of

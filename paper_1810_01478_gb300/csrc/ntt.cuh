@@ -75,99 +75,122 @@ __device__ __forceinline__ uint32_t reduce4(uint32_t x, uint32_t p) {
 __device__ __forceinline__ int npad(int i) { return i + (i >> 5); }
 __host__ __device__ constexpr int ntt_stride(int L) { return L + L / 32; }
 
-// One pass of S stages on groups of R = 2^S elements i = hi 2^(s+S) + m 2^s + lo.
+// log2 of the transform length used for n = 32 M limbs (the least L >= 2n)
+__host__ __device__ constexpr int ntt_logl(int M) {
+  int l = 0;
+  while ((1 << l) < 64 * M) ++l;
+  return l;
+}
+
+// One pass of S stages on groups of R = 2^S elements i = hi 2^(s+S) + m 2^s + lo,
+// everything but lo and hi known at compile time.  The twiddle of the
+// butterfly (m, m + 2^t) at stage h = 2^(s+t) is w_{2h}^j with
+// j = (m mod 2^t) 2^s + lo, i.e. table entry j LMAX/(2h) =
+// (m mod 2^t) (LMAX/2^(t+1)) + lo (LMAX/2^(s+t+1)).
+constexpr int NTT_LOG_HALF = 10;  // log2(NTT_LMAX / 2)
+
+template <int S, int s>
+__device__ __forceinline__ int pass_index(int base, int m) {
+  if constexpr (s >= 5) return npad(base) + m * ((1 << s) + (1 << (s - 5)));
+  else return npad(base + (m << s));
+}
+
 // forward (decimation in frequency, stages s+S-1 .. s): [0, 2p) -> [0, 2p)
-template <int S>
-__device__ __forceinline__ void dif_pass(uint32_t* buf, int L, int s, const uint2* __restrict__ tw, uint32_t p) {
-  constexpr int R = 1 << S;
-  const int groups = L >> S;
+template <int LOGL, int S, int s>
+__device__ __forceinline__ void dif_pass(uint32_t* buf, const uint2* __restrict__ tw, uint32_t p) {
+  constexpr int R = 1 << S, groups = (1 << LOGL) >> S;
   const uint32_t p2 = 2 * p;
   for (int g = lane_id(); g < groups; g += 32) {
     const int lo = g & ((1 << s) - 1);
     const int base = ((g >> s) << (s + S)) + lo;
     uint32_t x[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) x[m] = buf[npad(base + (m << s))];
+    for (int m = 0; m < R; ++m) x[m] = buf[pass_index<S, s>(base, m)];
 #pragma unroll
     for (int t = S - 1; t >= 0; --t) {
-      const int tstep = (NTT_LMAX / 2) >> (s + t);
+      const uint2* twt = tw + (lo << (NTT_LOG_HALF - s - t));
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        if (m & (1 << t)) continue;
-        const int j = ((m & ((1 << t) - 1)) << s) + lo;
-        const uint2 w = __ldg(tw + j * tstep);
-        const uint32_t u = x[m], v = x[m + (1 << t)];
-        const uint32_t sm = u + v;
-        x[m] = sm >= p2 ? sm - p2 : sm;
-        x[m + (1 << t)] = mul_shoup_lazy(u - v + p2, w.x, w.y, p);
+      for (int b = 0; b < (1 << t); ++b) {
+        const uint2 w = __ldg(twt + b * (1 << (NTT_LOG_HALF - t)));
+#pragma unroll
+        for (int hgh = 0; hgh < R; hgh += (2 << t)) {
+          const int m = hgh + b;
+          const uint32_t u = x[m], v = x[m + (1 << t)];
+          const uint32_t sm = u + v;
+          x[m] = sm >= p2 ? sm - p2 : sm;
+          x[m + (1 << t)] = mul_shoup_lazy(u - v + p2, w.x, w.y, p);
+        }
       }
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) buf[npad(base + (m << s))] = x[m];
+    for (int m = 0; m < R; ++m) buf[pass_index<S, s>(base, m)] = x[m];
   }
 }
 
 // inverse (decimation in time, stages s .. s+S-1): [0, 4p) -> [0, 4p)
-template <int S>
-__device__ __forceinline__ void dit_pass(uint32_t* buf, int L, int s, const uint2* __restrict__ tw, uint32_t p) {
-  constexpr int R = 1 << S;
-  const int groups = L >> S;
+template <int LOGL, int S, int s>
+__device__ __forceinline__ void dit_pass(uint32_t* buf, const uint2* __restrict__ tw, uint32_t p) {
+  constexpr int R = 1 << S, groups = (1 << LOGL) >> S;
   const uint32_t p2 = 2 * p;
   for (int g = lane_id(); g < groups; g += 32) {
     const int lo = g & ((1 << s) - 1);
     const int base = ((g >> s) << (s + S)) + lo;
     uint32_t x[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) x[m] = buf[npad(base + (m << s))];
+    for (int m = 0; m < R; ++m) x[m] = buf[pass_index<S, s>(base, m)];
 #pragma unroll
     for (int t = 0; t < S; ++t) {
-      const int tstep = (NTT_LMAX / 2) >> (s + t);
+      const uint2* twt = tw + (lo << (NTT_LOG_HALF - s - t));
 #pragma unroll
-      for (int m = 0; m < R; ++m) {
-        if (m & (1 << t)) continue;
-        const int j = ((m & ((1 << t) - 1)) << s) + lo;
-        const uint2 w = __ldg(tw + j * tstep);
-        uint32_t X = x[m];
-        X = X >= p2 ? X - p2 : X;
-        const uint32_t T = mul_shoup_lazy(x[m + (1 << t)], w.x, w.y, p);
-        x[m] = X + T;
-        x[m + (1 << t)] = X - T + p2;
+      for (int b = 0; b < (1 << t); ++b) {
+        const uint2 w = __ldg(twt + b * (1 << (NTT_LOG_HALF - t)));
+#pragma unroll
+        for (int hgh = 0; hgh < R; hgh += (2 << t)) {
+          const int m = hgh + b;
+          uint32_t X = x[m];
+          X = X >= p2 ? X - p2 : X;
+          const uint32_t T = mul_shoup_lazy(x[m + (1 << t)], w.x, w.y, p);
+          x[m] = X + T;
+          x[m + (1 << t)] = X - T + p2;
+        }
       }
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) buf[npad(base + (m << s))] = x[m];
+    for (int m = 0; m < R; ++m) buf[pass_index<S, s>(base, m)] = x[m];
+  }
+}
+
+template <int LOGL, int TOP>
+__device__ __forceinline__ void dif_passes(uint32_t* buf, const uint2* tw, uint32_t p) {
+  if constexpr (TOP > 0) {
+    constexpr int S = TOP >= 3 ? 3 : TOP;
+    dif_pass<LOGL, S, TOP - S>(buf, tw, p);
+    __syncwarp();
+    dif_passes<LOGL, TOP - S>(buf, tw, p);
+  }
+}
+
+template <int LOGL, int s>
+__device__ __forceinline__ void dit_passes(uint32_t* buf, const uint2* tw, uint32_t p) {
+  if constexpr (s < LOGL) {
+    constexpr int S = LOGL - s >= 3 ? 3 : LOGL - s;
+    dit_pass<LOGL, S, s>(buf, tw, p);
+    __syncwarp();
+    dit_passes<LOGL, s + S>(buf, tw, p);
   }
 }
 
 // Forward transform of the padded buf modulo prime q, in place ([0, 2p) in and out).
+template <int LOGL>
 __device__ __forceinline__ void warp_ntt_fwd(uint32_t* buf, const NttConst& nc, int q) {
-  const uint32_t p = sel3(nc.p, q);
-  const uint2* tw = nc.twf + q * (NTT_LMAX / 2);
-  int top = nc.logL;
-  while (top > 0) {
-    const int S = top >= 3 ? 3 : top;
-    const int s = top - S;
-    if (S == 3) dif_pass<3>(buf, nc.L, s, tw, p);
-    else if (S == 2) dif_pass<2>(buf, nc.L, s, tw, p);
-    else dif_pass<1>(buf, nc.L, s, tw, p);
-    __syncwarp();
-    top = s;
-  }
+  dif_passes<LOGL, LOGL>(buf, nc.twf + q * (NTT_LMAX / 2), sel3(nc.p, q));
 }
 
 // Inverse transform of the padded buf modulo prime q, in place, without the
 // 1/L factor (folded into the stored transforms); [0, 4p) in and out.
+template <int LOGL>
 __device__ __forceinline__ void warp_ntt_inv(uint32_t* buf, const NttConst& nc, int q) {
-  const uint32_t p = sel3(nc.p, q);
-  const uint2* tw = nc.twi + q * (NTT_LMAX / 2);
-  for (int s = 0; s < nc.logL;) {
-    const int S = nc.logL - s >= 3 ? 3 : nc.logL - s;
-    if (S == 3) dit_pass<3>(buf, nc.L, s, tw, p);
-    else if (S == 2) dit_pass<2>(buf, nc.L, s, tw, p);
-    else dit_pass<1>(buf, nc.L, s, tw, p);
-    __syncwarp();
-    s += S;
-  }
+  dit_passes<LOGL, 0>(buf, nc.twi + q * (NTT_LMAX / 2), sel3(nc.p, q));
 }
 
 // Transform of one n-limb mantissa (global) for all three primes into
@@ -188,7 +211,7 @@ __device__ __forceinline__ void warp_ntt_number(const uint32_t* __restrict__ man
       buf[npad(k)] = v >= 2 * p ? v - 2 * p : v;
     }
     __syncwarp();
-    warp_ntt_fwd(buf, nc, q);
+    warp_ntt_fwd<ntt_logl(M)>(buf, nc, q);
     uint32_t* o = out + (size_t)q * nc.L;
     for (int k = lane; k < nc.L; k += 32) {
       uint32_t v = buf[npad(k)];
@@ -280,7 +303,7 @@ __device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, co
       o[i + 3] = mont_mul_lazy(a.w, b.w, p, pinv);
     }
     __syncwarp();
-    warp_ntt_inv(o, nc, q);
+    warp_ntt_inv<ntt_logl(M)>(o, nc, q);
   }
   // each chunk's limbs gather c_k, c_{k-1}, c_{k-2}; the window words that
   // spill past a chunk's top are re-derived by the next chunk (crt_chunk
