@@ -205,15 +205,25 @@ def test_interlacing_and_precision_doubling():
 
 @pytest.mark.slow
 def test_table2_n500():
-    """Table 2 (Sec. 5.1), N = 500, beta = 1/2: printed lambda_1..3 to 1e-15."""
+    """Table 2 (Sec. 5.1), N = 500, beta = 1/2: printed lambda_1..3.
+
+    The paper rounds the k x k block of H^-1 to double before its eigensolve
+    (Sec. 4.5).  A backward-stable double eigensolver perturbs every
+    eigenvalue nu_m of that block by about eps * nu_1 in absolute terms, so
+    the printed lambda_m = 1/nu_m carries a relative error near
+    eps * lambda_m / lambda_1 (about 6e-14 for lambda_3 at N = 500); each
+    lambda_m is compared to max(1e-15, 8 eps lambda_m / lambda_1)."""
     with open(os.path.join(HERE, "golden", "table2_beta_half.json")) as f:
         row = json.load(f)["rows"][0]
     assert row["N"] == 500
     r = PL.run(Fraction(1, 2), 500, 8, 48)   # 1536 bits, k = 8
     with mpm.workprec(200):
+        eps = mpm.mpf(2) ** -52
+        lam1 = mpm.mpf(row["lambda"][0])
         for m in range(3):
             printed = mpm.mpf(row["lambda"][m])
-            assert abs(r["lambdas"][m] - printed) / printed < mpm.mpf("1e-15")
+            tol = max(mpm.mpf("1e-15"), 8 * eps * printed / lam1)
+            assert abs(r["lambdas"][m] - printed) / printed < tol
         # truncation errors: the paper casts the block to double before its
         # eigensolve (Sec. 4.5), so its lambda_1/lambda_2 errors (~1e-16,
         # 1e-14) carry double-precision noise of a few 1e-17; they are
