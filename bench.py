@@ -253,7 +253,8 @@ def run_ours(a):
                              peak_note=f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_LIMB_MAC} IMAD "
                                        f"per limb product x {sm_max:.0f} MHz (derived, not measured)"),
                phases_ms=dict(moments=prof["moments_ms"] / a.steps, ldlt=prof["ldlt_ms"] / a.steps,
-                              trailing=prof["trailing_ms"] / a.steps, invblock=prof["invblock_ms"] / a.steps,
+                              trailing=prof["trailing_ms"] / a.steps, scale=prof["scale_ms"] / a.steps,
+                              invblock=prof["invblock_ms"] / a.steps,
                               eig=prof["eig_ms"] / a.steps, grad=prof["grad_ms"] / a.steps),
                result=dict(lambda_f64=lam_f64, trunc_err_f64=lam[4].tolist(), dlambda_dbeta_f64=gr[3].tolist()[0]),
                clocks=clk)

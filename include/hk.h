@@ -142,8 +142,9 @@ HK_API hk_status hk_export(hk_ctx* ctx, int what, int64_t first, int64_t count, 
  *   [2] number of trailing-update launches
  *   [3] algorithmic limb products of those launches (n^2 per fused update)
  *   [4] moments ms, [5] LDL^T ms, [6] Algorithm 4 + block ms,
- *   [7] eigenvalues ms, [8] gradient ms */
-#define HK_PROFILE_FIELDS 9
+ *   [7] eigenvalues ms, [8] gradient ms,
+ *   [9] column scale (B_i) and its transforms within the LDL^T, ms */
+#define HK_PROFILE_FIELDS 10
 HK_API hk_status hk_set_profiling(hk_ctx* ctx, int on);
 HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 

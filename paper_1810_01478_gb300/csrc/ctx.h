@@ -58,6 +58,7 @@ struct Ctx {
   std::vector<cudaEvent_t> events;
   size_t ev_used = 0;
   std::vector<std::pair<size_t, size_t>> trail_ev;
+  std::vector<std::pair<size_t, size_t>> scale_ev;  // column scale + transforms of each step
   double trail_macs = 0.0;
   std::vector<std::pair<int, std::pair<size_t, size_t>>> stage_ev;  // (stage id, events)
   // eigen results (host copies, filled by the lambda stage)

@@ -472,6 +472,7 @@ hk_status hk_set_profiling(hk_ctx* h, int on) {
   c.prof = on != 0;
   c.ev_used = 0;
   c.trail_ev.clear();
+  c.scale_ev.clear();
   c.stage_ev.clear();
   c.trail_macs = 0.0;
   c.launches = 0;
@@ -499,6 +500,11 @@ hk_status hk_get_profile(hk_ctx* h, double* out, int cap) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c.events[p.second.first], c.events[p.second.second]);
     out[4 + p.first] += ms;
+  }
+  for (auto& p : c.scale_ev) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.events[p.first], c.events[p.second]);
+    out[9] += ms;
   }
   return HK_OK;
 }

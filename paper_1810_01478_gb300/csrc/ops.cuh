@@ -180,6 +180,7 @@ struct Ops {
       const int64_t T = rows * (rows + 1) / 2;
       cudaStreamWaitEvent(s, c.ev_recip, 0);  // R_i is ready
       const int gs = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, scale_res);
+      const size_t es = c.prof ? prof_mark(c) : 0;
       k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(c.A.view(), c.U.view(), N, i, c.rec, c.rec_meta, c.d_err);
       if (ntt) {  // transforms of U[i+1..N) and of B_i = A[i+1..N][i]
         const int g = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, fwd_res);
@@ -187,6 +188,7 @@ struct Ops {
         k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FB, nc, 1);
         count_launch(c, 2);
       }
+      if (c.prof) c.scale_ev.push_back({es, prof_mark(c)});
       // look-ahead: update d_{i+1} = A[i+1][i+1] first (entry t = 0 of the trailing triangle) ...
       const size_t e0 = c.prof ? prof_mark(c) : 0;
       trailing(i, 0, 1);
