@@ -65,6 +65,16 @@ __device__ __forceinline__ uint32_t sel3(const uint32_t (&a)[NTT_Q], int q) {
   return q == 0 ? a[0] : (q == 1 ? a[1] : a[2]);
 }
 
+// 16-byte read-only load that does not allocate in L1: the transforms stream
+// through once per product and would otherwise evict the twiddle table
+__device__ __forceinline__ uint4 ld_stream(const uint4* ptr) {
+  uint4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(ptr));
+  return v;
+}
+
 // [0, 4p) -> [0, p)
 __device__ __forceinline__ uint32_t reduce4(uint32_t x, uint32_t p) {
   x = x >= 2 * p ? x - 2 * p : x;
@@ -89,6 +99,29 @@ __host__ __device__ constexpr int ntt_logl(int M) {
 // (m mod 2^t) (LMAX/2^(t+1)) + lo (LMAX/2^(s+t+1)).
 constexpr int NTT_LOG_HALF = 10;  // log2(NTT_LMAX / 2)
 
+// Which groups the 32 lanes take together.  Group g of a pass has its low s
+// bits in lo and the rest in hi; lanes take g's bits [0, A) and [B, B + 5 - A)
+// and the iteration counter j the others.  A = B = 5 is the plain g = lane +
+// 32 j.  For the short strides 0 < s < 5 that order puts lanes 2^s words
+// apart and up to four of them in one bank; taking two of the lane bits from
+// hi's upper bits instead spreads the 32 lanes over all 32 banks of the
+// padded layout (A = s - 2, B = s, where the length allows).
+template <int LOGL, int S, int s>
+struct LaneMap {
+  static constexpr bool plain = s == 0 || s >= 5 || (1 << (LOGL - S)) < 32;
+  static constexpr int A = plain ? 5 : (s >= 2 ? s - 2 : 0);
+  static constexpr int B0 = LOGL - S - 5 + A;
+  static constexpr int B = plain ? 5 : (s < B0 ? (s < A ? A : s) : (B0 < A ? A : B0));
+  __device__ __forceinline__ static int group(int lane, int j) {
+    if constexpr (A == 5 && B == 5) {
+      return lane + 32 * j;
+    } else {
+      return (lane & ((1 << A) - 1)) | ((j & ((1 << (B - A)) - 1)) << A) | ((lane >> A) << B) |
+             ((j >> (B - A)) << (B + 5 - A));
+    }
+  }
+};
+
 template <int S, int s>
 __device__ __forceinline__ int pass_index(int base, int m) {
   if constexpr (s >= 5) return npad(base) + m * ((1 << s) + (1 << (s - 5)));
@@ -100,7 +133,10 @@ template <int LOGL, int S, int s>
 __device__ __forceinline__ void dif_pass(uint32_t* buf, const uint2* __restrict__ tw, uint32_t p) {
   constexpr int R = 1 << S, groups = (1 << LOGL) >> S;
   const uint32_t p2 = 2 * p;
-  for (int g = lane_id(); g < groups; g += 32) {
+  using LM = LaneMap<LOGL, S, s>;
+  const int lane = lane_id();
+  for (int g0 = lane; g0 < groups; g0 += 32) {
+    const int g = LM::plain ? g0 : LM::group(lane, g0 >> 5);
     const int lo = g & ((1 << s) - 1);
     const int base = ((g >> s) << (s + S)) + lo;
     uint32_t x[R];
@@ -132,7 +168,10 @@ template <int LOGL, int S, int s>
 __device__ __forceinline__ void dit_pass(uint32_t* buf, const uint2* __restrict__ tw, uint32_t p) {
   constexpr int R = 1 << S, groups = (1 << LOGL) >> S;
   const uint32_t p2 = 2 * p;
-  for (int g = lane_id(); g < groups; g += 32) {
+  using LM = LaneMap<LOGL, S, s>;
+  const int lane = lane_id();
+  for (int g0 = lane; g0 < groups; g0 += 32) {
+    const int g = LM::plain ? g0 : LM::group(lane, g0 >> 5);
     const int lo = g & ((1 << s) - 1);
     const int base = ((g >> s) << (s + S)) + lo;
     uint32_t x[R];
@@ -295,7 +334,7 @@ __device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, co
     const uint4* b4 = reinterpret_cast<const uint4*>(fy + (size_t)q * L);
     uint32_t* o = nb + q * st;
     for (int k = lane; k < L / 4; k += 32) {
-      const uint4 a = a4[k], b = b4[k];
+      const uint4 a = ld_stream(a4 + k), b = ld_stream(b4 + k);
       const int i = npad(4 * k);  // the four words share one padding block
       o[i] = mont_mul_lazy(a.x, b.x, p, pinv);
       o[i + 1] = mont_mul_lazy(a.y, b.y, p, pinv);
