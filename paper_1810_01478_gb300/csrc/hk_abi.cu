@@ -42,10 +42,10 @@ bool use_ntt(int M) {
 }
 
 namespace {
-// three primes k 2^e + 1 below 2^30 (e = 20, 21, 23; p1 > p2 > p3, p1 < 2 p3)
-// with primitive roots 7, 5, 3
-constexpr uint32_t kPrimes[NTT_Q] = {1053818881u, 1012924417u, 998244353u};
-constexpr uint32_t kGen[NTT_Q] = {7u, 5u, 3u};
+// the three largest primes k 3 2^11 + 1 below 2^30 (p1 > p2 > p3, p1 < 2 p3)
+// with primitive roots 23, 5, 10
+constexpr uint32_t kPrimes[NTT_Q] = {1073707009u, 1073682433u, 1073651713u};
+constexpr uint32_t kGen[NTT_Q] = {23u, 5u, 10u};
 
 uint32_t pow_mod(uint64_t b, uint64_t e, uint32_t p) {
   uint64_t r = 1;
@@ -97,16 +97,16 @@ NttConst ntt_const(int n) {
     nc.twf = t.twf;
     nc.twi = t.twi;
   }
-  int L = 1, logL = 0;
-  while (L < 2 * n) {
-    L <<= 1;
-    ++logL;
-  }
+  const int L = ntt_len(n);
   nc.L = L;
-  nc.logL = logL;
+  nc.logL = ntt_logk(n);
   for (int q = 0; q < NTT_Q; ++q) {
     const uint32_t p = kPrimes[q];
     nc.p[q] = p;
+    nc.w3[q] = pow_mod(kGen[q], (p - 1) / 3, p);
+    nc.w3s[q] = shoup(nc.w3[q], p);
+    nc.w3i[q] = inv_mod(nc.w3[q], p);
+    nc.w3is[q] = shoup(nc.w3i[q], p);
     uint32_t x = p;  // Newton: x = p^{-1} mod 2^32
     for (int it = 0; it < 5; ++it) x *= 2u - p * x;
     nc.pinv[q] = 0u - x;

@@ -261,6 +261,7 @@ __device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, co
                                             int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
                                             const uint32_t* amant, int sa_sgn, int ea, uint32_t (&out)[M]) {
   constexpr int n = 32 * M;
+  static_assert(WarpSmem<M>::words <= NTT_Q * ntt_stride(ntt_len(n)), "combine frame exceeds the NTT buffer");
   const bool p_zero = x_zero || y_zero;
   uint32_t lo[M], hi[M];
   if (!p_zero) {
@@ -277,8 +278,13 @@ __device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, co
 
 // The trailing update of step i with NTT products.  FU[c - i - 1], FB[r - i - 1]
 // hold the transforms of U[c] (unscaled) and B_i[r] (scaled) for this step.
+// Blocks of HK_NTT_TRAIL_WARPS warps, two resident per SM: at 768 limbs a warp
+// needs 19 KB of shared memory, so 2 x 6 warps fill the SM's 228 KB.
+#ifndef HK_NTT_TRAIL_WARPS
+#define HK_NTT_TRAIL_WARPS 6
+#endif
 template <int M>
-__global__ void __launch_bounds__(128) k_trailing_ntt(MPVec A, MPVec U, const uint32_t* __restrict__ FU,
+__global__ void __launch_bounds__(32 * HK_NTT_TRAIL_WARPS, 2) k_trailing_ntt(MPVec A, MPVec U, const uint32_t* __restrict__ FU,
                                                       const uint32_t* __restrict__ FB, int N, int i, int64_t t0,
                                                       int64_t t1, NttConst nc, const int* err) {
   constexpr int n = 32 * M;

@@ -7,12 +7,19 @@
 // length L >= 2n computed modulo each prime and recombined by the Chinese
 // remainder theorem (Garner's form) gives every c_t exactly, and the exact
 // product is sum_t c_t 2^(32 t).  Every prime is below 2^30 and has the form
-// k 2^e + 1 with e >= 20, so power-of-two lengths up to 2^20 have roots of
-// unity.
+// k 3 2^11 + 1, so lengths 2^a and 3 2^a (a <= 11) have roots of unity.
 //
-// Layout: transforms of length L are kept in bit-reversed order (forward:
-// decimation in frequency, natural -> bit-reversed; inverse: decimation in
-// time, bit-reversed -> natural), so pointwise products need no reordering.
+// Length: the least L = 2^a or L = 3 K (K = 2^a) with L >= 2n; 3 K saves a
+// quarter of the work and memory when 2n is 3 2^a (1536 at n = 768, 768 at
+// n = 384).  With gcd(3, K) = 1 the index map t -> (t mod 3, t mod K) turns
+// the cyclic convolution of length 3 K into a two-dimensional one of size
+// 3 x K (Good-Thomas), whose transform is three length-K transforms (rows)
+// and K three-point transforms (columns), with no twiddles between them.
+// Row r of the 3 x K array is held at positions r K .. r K + K - 1.
+//
+// Layout: rows are kept in bit-reversed order (forward: decimation in
+// frequency, natural -> bit-reversed; inverse: decimation in time,
+// bit-reversed -> natural), so pointwise products need no reordering.
 // Twiddle factors w^k (k < LMAX/2, w a primitive LMAX-th root) and their
 // inverses live in a device table with Shoup companions floor(w 2^32 / p).
 //
@@ -26,16 +33,18 @@
 namespace hk {
 
 constexpr int NTT_Q = 3;
-constexpr int NTT_LMAX = 2048;  // transform length limit: n <= 1024 limbs
+constexpr int NTT_LMAX = 2048;  // power-of-two length limit: n <= 1024 limbs
 
 struct NttConst {
   uint32_t p[NTT_Q], pinv[NTT_Q];  // primes, -p^{-1} mod 2^32 (Montgomery)
   uint32_t rl[NTT_Q], rls[NTT_Q];  // 2^32 / L mod p and its Shoup companion
+  uint32_t w3[NTT_Q], w3s[NTT_Q];  // a primitive cube root of unity mod p (+ Shoup)
+  uint32_t w3i[NTT_Q], w3is[NTT_Q];  // its inverse (+ Shoup)
   uint32_t i12, i12s, i13, i13s, i23, i23s;  // p1^{-1} mod p2, p1^{-1} mod p3, p2^{-1} mod p3 (+ Shoup)
   uint64_t p12;                    // p1 p2
   const uint2* twf;                // [q][k]: (w^k, Shoup), k < LMAX/2
   const uint2* twi;                // [q][k]: (w^-k, Shoup)
-  int L, logL;
+  int L, logL;                     // transform length and log2 of its row length
 };
 
 __device__ __forceinline__ uint32_t mod_add(uint32_t a, uint32_t b, uint32_t p) {
@@ -85,11 +94,27 @@ __device__ __forceinline__ uint32_t reduce4(uint32_t x, uint32_t p) {
 __device__ __forceinline__ int npad(int i) { return i + (i >> 5); }
 __host__ __device__ constexpr int ntt_stride(int L) { return L + L / 32; }
 
-// log2 of the transform length used for n = 32 M limbs (the least L >= 2n)
-__host__ __device__ constexpr int ntt_logl(int M) {
+// Transform shape for n limbs: L = rows 2^logk, rows in {1, 3}, the least
+// such L >= 2n (ties go to the power of two).
+__host__ __device__ constexpr int ntt_log2_ceil(int x) {
   int l = 0;
-  while ((1 << l) < 64 * M) ++l;
+  while ((1 << l) < x) ++l;
   return l;
+}
+__host__ __device__ constexpr int ntt_rows(int n) {
+  return (3 << ntt_log2_ceil((2 * n + 2) / 3)) < (1 << ntt_log2_ceil(2 * n)) ? 3 : 1;
+}
+__host__ __device__ constexpr int ntt_logk(int n) {
+  return ntt_rows(n) == 3 ? ntt_log2_ceil((2 * n + 2) / 3) : ntt_log2_ceil(2 * n);
+}
+__host__ __device__ constexpr int ntt_len(int n) { return ntt_rows(n) << ntt_logk(n); }
+
+// position of coefficient t (< L) in the rows x K array
+template <int n>
+__device__ __forceinline__ int ntt_pos(int t) {
+  constexpr int K = 1 << ntt_logk(n);
+  if constexpr (ntt_rows(n) == 1) return t;
+  else return (t % 3) * K + (t & (K - 1));
 }
 
 // One pass of S stages on groups of R = 2^S elements i = hi 2^(s+S) + m 2^s + lo,
@@ -219,17 +244,64 @@ __device__ __forceinline__ void dit_passes(uint32_t* buf, const uint2* tw, uint3
   }
 }
 
-// Forward transform of the padded buf modulo prime q, in place ([0, 2p) in and out).
-template <int LOGL>
+// Three-point transforms of the K columns (a, b, c) = rows 0, 1, 2 at
+// position j, with w a primitive cube root of unity (w^2 = -1 - w):
+//   X0 = a + b + c,  X1 = (a - c) + w (b - c),  X2 = (a - b) - w (b - c).
+// Inputs in [0, 2p), outputs in [0, 2p).
+template <int K>
+__device__ __forceinline__ void warp_dft3(uint32_t* buf, uint32_t w, uint32_t ws, uint32_t p) {
+  constexpr int st = ntt_stride(K);
+  const uint32_t p2 = 2 * p;
+  for (int j = lane_id(); j < K; j += 32) {
+    const int i = npad(j);
+    uint32_t a = buf[i], b = buf[st + i], c = buf[2 * st + i];
+    a = a >= p ? a - p : a;
+    b = b >= p ? b - p : b;
+    c = c >= p ? c - p : c;
+    const uint32_t m = mul_shoup_lazy(b - c + p, w, ws, p);  // [0, 2p)
+    uint32_t x0 = a + b + c;                                 // [0, 3p)
+    uint32_t x1 = a - c + p + m;                             // [0, 4p)
+    uint32_t x2 = a - b + 3 * p - m;                         // (0, 4p)
+    x0 = x0 >= p2 ? x0 - p2 : x0;
+    x1 = x1 >= p2 ? x1 - p2 : x1;
+    x2 = x2 >= p2 ? x2 - p2 : x2;
+    buf[i] = x0;
+    buf[st + i] = x1;
+    buf[2 * st + i] = x2;
+  }
+}
+
+// Forward transform of the padded buf (rows x 2^LOGK) modulo prime q, in
+// place ([0, 2p) in and out): rows first, then columns.
+template <int LOGK, int ROWS>
 __device__ __forceinline__ void warp_ntt_fwd(uint32_t* buf, const NttConst& nc, int q) {
-  dif_passes<LOGL, LOGL>(buf, nc.twf + q * (NTT_LMAX / 2), sel3(nc.p, q));
+  const uint32_t p = sel3(nc.p, q);
+#pragma unroll 1
+  for (int r = 0; r < ROWS; ++r) {
+    dif_passes<LOGK, LOGK>(buf + r * ntt_stride(1 << LOGK), nc.twf + q * (NTT_LMAX / 2), p);
+    __syncwarp();
+  }
+  if constexpr (ROWS == 3) {
+    warp_dft3<1 << LOGK>(buf, sel3(nc.w3, q), sel3(nc.w3s, q), p);
+    __syncwarp();
+  }
 }
 
 // Inverse transform of the padded buf modulo prime q, in place, without the
-// 1/L factor (folded into the stored transforms); [0, 4p) in and out.
-template <int LOGL>
+// 1/L factor (folded into the stored transforms): columns first, then rows;
+// [0, 2p) in, [0, 4p) out.
+template <int LOGK, int ROWS>
 __device__ __forceinline__ void warp_ntt_inv(uint32_t* buf, const NttConst& nc, int q) {
-  dit_passes<LOGL, 0>(buf, nc.twi + q * (NTT_LMAX / 2), sel3(nc.p, q));
+  const uint32_t p = sel3(nc.p, q);
+  if constexpr (ROWS == 3) {
+    warp_dft3<1 << LOGK>(buf, sel3(nc.w3i, q), sel3(nc.w3is, q), p);
+    __syncwarp();
+  }
+#pragma unroll 1
+  for (int r = 0; r < ROWS; ++r) {
+    dit_passes<LOGK, 0>(buf + r * ntt_stride(1 << LOGK), nc.twi + q * (NTT_LMAX / 2), p);
+    __syncwarp();
+  }
 }
 
 // Transform of one n-limb mantissa (global) for all three primes into
@@ -244,13 +316,13 @@ __device__ __forceinline__ void warp_ntt_number(const uint32_t* __restrict__ man
 #pragma unroll 1
   for (int q = 0; q < NTT_Q; ++q) {
     const uint32_t p = sel3(nc.p, q), rl = sel3(nc.rl, q), rls = sel3(nc.rls, q);
-    for (int k = lane; k < nc.L; k += 32) {
+    for (int k = lane; k < ntt_len(n); k += 32) {
       uint32_t v = k < n ? mant[k] : 0u;
       v = v >= 2 * p ? v - 2 * p : v;  // 2^32 < 4p: now in [0, 2p)
-      buf[npad(k)] = v >= 2 * p ? v - 2 * p : v;
+      buf[npad(ntt_pos<n>(k))] = v >= 2 * p ? v - 2 * p : v;
     }
     __syncwarp();
-    warp_ntt_fwd<ntt_logl(M)>(buf, nc, q);
+    warp_ntt_fwd<ntt_logk(n), ntt_rows(n)>(buf, nc, q);
     uint32_t* o = out + (size_t)q * nc.L;
     for (int k = lane; k < nc.L; k += 32) {
       uint32_t v = buf[npad(k)];
@@ -278,34 +350,56 @@ __device__ __forceinline__ void crt3(uint32_t r1, uint32_t r2, uint32_t r3, cons
   w2 = (uint32_t)(v >> 64);
 }
 
-// Product limbs of one chunk [k0, k0 + M) from the residues res[q * L + t]
-// (natural order, c_t = 0 outside [0, 2n-1)); returns the carry out (<= 3).
-template <int M>
-__device__ __forceinline__ uint32_t crt_chunk(const uint32_t* res, int k0, const NttConst& nc, uint32_t (&out)[M]) {
-  constexpr int n = 32 * M;
-  const int st = ntt_stride(nc.L);
+// Garner's recombination in place: at every position of the three prime
+// buffers the residues of one c_t (each in [0, 4p)) become the three 32-bit
+// words of c_t.  A loop over positions, so its code stays small.
+template <int n>
+__device__ __forceinline__ void crt_in_place(uint32_t* res, const NttConst& nc) {
+  constexpr int L = ntt_len(n), st = ntt_stride(L);
   const uint32_t p1 = nc.p[0], p2 = nc.p[1], p3 = nc.p[2];
-  uint32_t a1 = 0, a2 = 0, b2 = 0;  // w1(c_{k-1}), w2(c_{k-1}), w2(c_{k-2}) carried along
-  // prime the window with c_{k0-2} and c_{k0-1}
-#pragma unroll
-  for (int d = 2; d >= 1; --d) {
-    const int t = k0 - d;
-    uint32_t w0 = 0, w1 = 0, w2 = 0;
-    if (t >= 0 && t < 2 * n - 1)
-      crt3(reduce4(res[npad(t)], p1), reduce4(res[st + npad(t)], p2), reduce4(res[2 * st + npad(t)], p3), nc, w0, w1,
-           w2);
-    b2 = a2;
-    a1 = w1;
-    a2 = w2;
+#pragma unroll 1
+  for (int k = lane_id(); k < L; k += 32) {
+    const int i = npad(k);
+    uint32_t w0, w1, w2;
+    crt3(reduce4(res[i], p1), reduce4(res[st + i], p2), reduce4(res[2 * st + i], p3), nc, w0, w1, w2);
+    res[i] = w0;
+    res[st + i] = w1;
+    res[2 * st + i] = w2;
+  }
+}
+
+// Product limbs of one chunk [k0, k0 + M) from the words of crt_in_place:
+// limb k = w0(c_k) + w1(c_{k-1}) + w2(c_{k-2}) + carry; returns the carry
+// out (<= 3).  The window words of c_{k0-2}, c_{k0-1} are re-read here, so
+// only carries cross chunks.
+template <int M>
+__device__ __forceinline__ uint32_t crt_chunk(const uint32_t* W, int k0, uint32_t (&out)[M]) {
+  constexpr int n = 32 * M;
+  constexpr int st = ntt_stride(ntt_len(n));
+  constexpr int K = 1 << ntt_logk(n);
+  const int r0 = ntt_rows(n) == 3 ? k0 % 3 : 0;
+  // position of coefficient k0 + d (d >= -2 at compile time), c = 0 below 0
+  auto at = [&](int d) -> int {
+    if constexpr (ntt_rows(n) == 1) {
+      return npad(k0 + d);
+    } else {
+      int r = r0 + ((d % 3) + 3) % 3;
+      r = r >= 3 ? r - 3 : r;
+      return npad(r * K + ((k0 + d) & (K - 1)));
+    }
+  };
+  uint32_t a1 = 0, a2 = 0, b2 = 0;  // w1(c_{k-1}), w2(c_{k-1}), w2(c_{k-2})
+  if (k0 >= 2) b2 = W[2 * st + at(-2)];
+  if (k0 >= 1) {
+    const int q = at(-1);
+    a1 = W[st + q];
+    a2 = W[2 * st + q];
   }
   uint64_t carry = 0;
 #pragma unroll
   for (int kk = 0; kk < M; ++kk) {
-    const int t = k0 + kk;
-    uint32_t w0 = 0, w1 = 0, w2 = 0;
-    if (t < 2 * n - 1)
-      crt3(reduce4(res[npad(t)], p1), reduce4(res[st + npad(t)], p2), reduce4(res[2 * st + npad(t)], p3), nc, w0, w1,
-           w2);
+    const int q = at(kk);
+    const uint32_t w0 = W[q], w1 = W[st + q], w2 = W[2 * st + q];
     const uint64_t s = (uint64_t)w0 + a1 + b2 + carry;
     out[kk] = (uint32_t)s;
     carry = s >> 32;
@@ -313,7 +407,6 @@ __device__ __forceinline__ uint32_t crt_chunk(const uint32_t* res, int k0, const
     a1 = w1;
     a2 = w2;
   }
-  // the window's leftover words of c_{k0+M-1}, c_{k0+M-2} belong to the next chunk
   return (uint32_t)carry;
 }
 
@@ -342,13 +435,12 @@ __device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, co
       o[i + 3] = mont_mul_lazy(a.w, b.w, p, pinv);
     }
     __syncwarp();
-    warp_ntt_inv<ntt_logl(M)>(o, nc, q);
+    warp_ntt_inv<ntt_logk(n), ntt_rows(n)>(o, nc, q);
   }
-  // each chunk's limbs gather c_k, c_{k-1}, c_{k-2}; the window words that
-  // spill past a chunk's top are re-derived by the next chunk (crt_chunk
-  // primes its window from c_{k0-2}, c_{k0-1}), so only carries cross lanes
-  uint32_t loc = crt_chunk<M>(nb, lane * M, nc, lo);
-  uint32_t hic = crt_chunk<M>(nb, n + lane * M, nc, hi);
+  crt_in_place<n>(nb, nc);
+  __syncwarp();
+  uint32_t loc = crt_chunk<M>(nb, lane * M, lo);
+  uint32_t hic = crt_chunk<M>(nb, n + lane * M, hi);
   __syncwarp();
   for (int it = 0; it < 70; ++it) {
     uint32_t cin_lo = __shfl_up_sync(FULL, loc, 1);

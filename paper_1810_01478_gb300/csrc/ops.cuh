@@ -40,6 +40,7 @@ template <int M>
 struct Ops {
   static constexpr int n = 32 * M;
   static constexpr int WARPS = 4;  // warps per block of the warp-per-number kernels
+  static constexpr int NTW = HK_NTT_TRAIL_WARPS;  // warps per block of k_trailing_ntt
   static constexpr size_t fused_smem = (size_t)WARPS * WarpSmem<M>::words * 4;
   static constexpr size_t div_smem = (size_t)WARPS * (4 * n + 4) * 4;
   static constexpr size_t recip_smem = (size_t)(3 * n + 4) * 4;
@@ -135,12 +136,17 @@ struct Ops {
         if ((st = check_cuda(c, cudaMalloc(&c.ntt_buf, need * 4), "allocating the transforms")) != HK_OK) return st;
         c.ntt_cap = need;
       }
-      ntt_smem = (size_t)WARPS * NTT_Q * ntt_stride(nc.L) * 4;
+      ntt_smem = (size_t)NTW * NTT_Q * ntt_stride(nc.L) * 4;
       fwd_smem = (size_t)WARPS * ntt_stride(nc.L) * 4;
-      if ((st = check_cuda(c, allow_smem_blocks(k_trailing_ntt<M>, ntt_smem, 2), "smem attribute")) ||
+      if ((st = check_cuda(c, allow_smem(k_trailing_ntt<M>, ntt_smem), "smem attribute")) ||
           (st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fwd_smem), "smem attribute")))
         return st;
-      ntt_res = resident_blocks(k_trailing_ntt<M>, 32 * WARPS, ntt_smem, c.device);
+      // as many blocks as registers allow, the rest of the SM's memory to L1
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_trailing_ntt<M>, 32 * NTW, ntt_smem);
+      if ((st = check_cuda(c, allow_smem_blocks(k_trailing_ntt<M>, ntt_smem, std::max(per_sm, 1)), "smem attribute")))
+        return st;
+      ntt_res = resident_blocks(k_trailing_ntt<M>, 32 * NTW, ntt_smem, c.device);
       fwd_res = resident_blocks(k_ntt_fwd<M>, 32 * WARPS, fwd_smem, c.device);
     }
     uint32_t* FU = c.ntt_buf;
@@ -148,8 +154,8 @@ struct Ops {
     auto trailing = [&](int i, int64_t t0, int64_t t1) {
       const int64_t cnt = t1 - t0;
       if (ntt) {
-        const int g = (int)std::min<int64_t>((cnt + WARPS - 1) / WARPS, ntt_res);
-        k_trailing_ntt<M><<<g, 32 * WARPS, ntt_smem, c.stream>>>(c.A.view(), c.U.view(), FU, FB, N, i, t0, t1, nc,
+        const int g = (int)std::min<int64_t>((cnt + NTW - 1) / NTW, ntt_res);
+        k_trailing_ntt<M><<<g, 32 * NTW, ntt_smem, c.stream>>>(c.A.view(), c.U.view(), FU, FB, N, i, t0, t1, nc,
                                                                    c.d_err);
       } else {
         const int g = (int)std::min<int64_t>((cnt + WARPS - 1) / WARPS, trail_res);

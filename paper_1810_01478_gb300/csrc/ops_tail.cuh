@@ -27,11 +27,6 @@ static double to_double(int32_t s, int32_t e, const uint32_t* m, int n) {
   return s ? -r : r;
 }
 
-static int ntt_const_L(int n) {
-  int L = 1;
-  while (L < 2 * n) L <<= 1;
-  return L;
-}
 
 template <int M>
 struct Tail {
@@ -161,7 +156,7 @@ struct Tail {
       k_x_init<M><<<grid, 256, 0, c.stream>>>(c.X.view(), N, k);
       count_launch(c);
     }
-    const bool ntt = use_ntt(M) && c.ntt_buf && c.ntt_cap >= 2 * (size_t)NTT_Q * ntt_const_L(n) * N;
+    const bool ntt = use_ntt(M) && c.ntt_buf && c.ntt_cap >= 2 * (size_t)NTT_Q * ntt_len(n) * N;
     if (ntt) {
       // Algorithm 4 with NTT products: per step, the transforms of the pivot
       // column L[i+1..N)[i] (unscaled) and of the finished row X[i][0..cols) (scaled)

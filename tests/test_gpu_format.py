@@ -29,7 +29,7 @@ SCHOOLBOOK, NTT = 1, 2
 
 
 @pytest.mark.parametrize("product_algorithm", [SCHOOLBOOK, NTT], indirect=True)
-@pytest.mark.parametrize("M", [1, 2, 4, 7, 24])
+@pytest.mark.parametrize("M", [1, 2, 3, 4, 5, 7, 12, 16, 24])
 def test_fused_batch_bit_exact(M, product_algorithm):
     import torch
     import paper_1810_01478_gb300 as hk

@@ -49,7 +49,8 @@ def test_moments_bit_exact(beta, N, bits):
 
 
 @pytest.mark.parametrize("product_algorithm", [1, 2], indirect=True)
-@pytest.mark.parametrize("N,bits", [(48, 4096), (1, 4096), (2, 1024), (33, 1024), (20, 24576), (40, 8192)])
+@pytest.mark.parametrize("N,bits", [(48, 4096), (1, 4096), (2, 1024), (33, 1024), (20, 24576), (40, 8192),
+                                    (30, 12288), (25, 3072)])
 def test_ldlt_beta_half_bit_exact(N, bits, product_algorithm):
     import paper_1810_01478_gb300 as hk
     n = bits // 32
