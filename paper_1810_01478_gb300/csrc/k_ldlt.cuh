@@ -261,19 +261,19 @@ __device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, co
                                             int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
                                             const uint32_t* amant, int sa_sgn, int ea, uint32_t (&out)[M]) {
   constexpr int n = 32 * M;
-  static_assert(WarpSmem<M>::words <= NTT_Q * ntt_stride(ntt_len(n)), "combine frame exceeds the NTT buffer");
+  static_assert(WarpSmemPad<M>::words <= NTT_Q * ntt_stride(ntt_len(n)), "combine frame exceeds the NTT buffer");
   const bool p_zero = x_zero || y_zero;
   uint32_t lo[M], hi[M];
   if (!p_zero) {
     warp_mul_ntt<M>(fx, fy, nb, nc, lo, hi);
     __syncwarp();  // every lane has read the residues before the region is reused
   }
-  WarpSmem<M> sm(nb);
-  if (!p_zero) stage_product<M>(sm.sp, lo, hi);
-  copy_to_smem<M>(sm.sa, amant);
+  WarpSmemPad<M> sm(nb);
+  if (!p_zero) stage_product<M, IxPad>(sm.sp, lo, hi);
+  copy_to_smem<M, IxPad>(sm.sa, amant);
   __syncwarp();
-  const bool a_zero = sm.sa[n - 1] == 0u;
-  return sub_product<M>(sm, sa_sgn, ea, a_zero, sx ^ sy, ex + ey, p_zero, out);
+  const bool a_zero = sm.sa[IxPad::at(n - 1)] == 0u;
+  return sub_product<M, IxPad>(sm, sa_sgn, ea, a_zero, sx ^ sy, ex + ey, p_zero, out);
 }
 
 // The trailing update of step i with NTT products.  FU[c - i - 1], FB[r - i - 1]

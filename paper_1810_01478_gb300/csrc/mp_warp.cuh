@@ -147,13 +147,27 @@ __device__ __forceinline__ void store_chunk(uint32_t* __restrict__ dst, const ui
   }
 }
 
+// Index policies for a warp's staging areas in shared memory.  IxPlain puts
+// word i at i.  IxPad leaves one spare word after every 32 (word i at
+// i + i/32).  Lane l's chunk starts at word l M, so under IxPlain the lanes
+// of one access fall into only 32/gcd(M, 32) banks (4 at M = 24, 2 at
+// M = 16); under IxPad at most two lanes share a bank for M <= 32.
+struct IxPlain {
+  __host__ __device__ static constexpr int at(int i) { return i; }
+  __host__ __device__ static constexpr int words(int w) { return w; }
+};
+struct IxPad {
+  __host__ __device__ static constexpr int at(int i) { return i + (i >> 5); }
+  __host__ __device__ static constexpr int words(int w) { return w + (w + 31) / 32; }
+};
+
 // smem copy of a whole n-limb mantissa by the warp (n = 32 M)
-template <int M>
+template <int M, class IX = IxPlain>
 __device__ __forceinline__ void copy_to_smem(uint32_t* dst, const uint32_t* __restrict__ src) {
   uint32_t v[M];
   load_chunk<M>(src, v);
 #pragma unroll
-  for (int k = 0; k < M; ++k) dst[lane_id() * M + k] = v[k];
+  for (int k = 0; k < M; ++k) dst[IX::at(lane_id() * M + k)] = v[k];
 }
 
 // ---------------------------------------------------------------------------
@@ -288,12 +302,12 @@ struct Staged {
   int off, len;
 };
 
-template <int M>
+template <int M, class IX = IxPlain>
 __device__ __forceinline__ void frame_chunk(const Staged& s, int c, uint32_t (&v)[M]) {
 #pragma unroll
   for (int k = 0; k < M; ++k) {
     const int i = c * M + k - s.off;
-    if (s.p) v[k] = (i >= 0 && i < s.len) ? s.p[i] : 0u;
+    if (s.p) v[k] = (i >= 0 && i < s.len) ? s.p[IX::at(i)] : 0u;
     else v[k] = (i == 0) ? 1u : 0u;
   }
 }
@@ -314,7 +328,7 @@ struct Result {
 // between 0 and the larger operand's last-limb weight gives the same
 // truncated result (the larger one is a multiple of that weight, and the
 // result's own last limb is at most one limb lower), so the stand-in is exact.
-template <int M>
+template <int M, class IX = IxPlain>
 __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged& Y, int sY, int base,
                                           uint32_t* fr, uint32_t (&out)[M]) {
   constexpr int n = 32 * M;
@@ -327,8 +341,8 @@ __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged&
 #pragma unroll
     for (int grp = 0; grp < 3; ++grp) {
       uint32_t xv[M], yv[M];
-      frame_chunk<M>(X, grp * 32 + lane, xv);
-      frame_chunk<M>(Y, grp * 32 + lane, yv);
+      frame_chunk<M, IX>(X, grp * 32 + lane, xv);
+      frame_chunk<M, IX>(Y, grp * 32 + lane, yv);
       g[grp] = chunk_add<M>(r[grp], xv, yv) != 0;
       p[grp] = !g[grp] && chunk_is_ones<M>(r[grp]);
     }
@@ -345,8 +359,8 @@ __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged&
 #pragma unroll
     for (int grp = 0; grp < 3; ++grp) {
       uint32_t xv[M], yv[M];
-      frame_chunk<M>(X, grp * 32 + lane, xv);
-      frame_chunk<M>(Y, grp * 32 + lane, yv);
+      frame_chunk<M, IX>(X, grp * 32 + lane, xv);
+      frame_chunk<M, IX>(Y, grp * 32 + lane, yv);
       g[grp] = chunk_sub<M>(r[grp], xv, yv) != 0;
       p[grp] = !g[grp] && chunk_is_zero<M>(r[grp]);
     }
@@ -406,14 +420,14 @@ __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged&
 #pragma unroll
   for (int grp = 0; grp < 3; ++grp)
 #pragma unroll
-    for (int k = 0; k < M; ++k) fr[(grp * 32 + lane) * M + k] = r[grp][k];
-  if (lane == 0) fr[3 * n] = top;
+    for (int k = 0; k < M; ++k) fr[IX::at((grp * 32 + lane) * M + k)] = r[grp][k];
+  if (lane == 0) fr[IX::at(3 * n)] = top;
   __syncwarp();
   const int lowest = T - n + 1;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
     const int i = lowest + lane * M + k;
-    out[k] = (i >= 0) ? fr[i] : 0u;
+    out[k] = (i >= 0) ? fr[IX::at(i)] : 0u;
   }
   __syncwarp();
   res.sgn = rs;
@@ -439,15 +453,28 @@ struct WarpSmem {
   __device__ explicit WarpSmem(uint32_t* base) : ys(base), sa(base + n), sp(base + 2 * n + 2) {}
 };
 
-// Stage the product (lo/hi chunks) into sp.
+// The same areas under IxPad (no ys): sa at logical word n, sp at 2n + 32,
+// both multiples of 32, so that sa[IxPad::at(i)] and sp[IxPad::at(i)] are
+// the logical words n + i and 2n + 32 + i of the padded region, and the
+// combine frame (3n + 1 words from sa) stays inside it.
 template <int M>
+struct WarpSmemPad {
+  static constexpr int n = 32 * M;
+  static constexpr int words = IxPad::words(4 * n + 32);
+  uint32_t* sa;
+  uint32_t* sp;
+  __device__ explicit WarpSmemPad(uint32_t* base) : sa(base + IxPad::at(n)), sp(base + IxPad::at(2 * n + 32)) {}
+};
+
+// Stage the product (lo/hi chunks) into sp.
+template <int M, class IX = IxPlain>
 __device__ __forceinline__ void stage_product(uint32_t* sp, const uint32_t (&lo)[M], const uint32_t (&hi)[M]) {
   constexpr int n = 32 * M;
   const int lane = lane_id();
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    sp[lane * M + k] = lo[k];
-    sp[n + lane * M + k] = hi[k];
+    sp[IX::at(lane * M + k)] = lo[k];
+    sp[IX::at(n + lane * M + k)] = hi[k];
   }
 }
 
@@ -472,15 +499,15 @@ __device__ __forceinline__ int product_top(const uint32_t (&lo)[M], const uint32
 // trunc_n(a - P) where P = (product in sp, 2n limbs, exponent ep, sign sp_sgn)
 // and a = (sa staged n limbs, sign sa_sgn, exponent ea, a_zero).  Chooses the
 // frame placement described at combine().
-template <int M>
-__device__ __forceinline__ Result sub_product(const WarpSmem<M>& sm, int sa_sgn, int ea, bool a_zero,
+template <int M, class IX = IxPlain, class SMEM>
+__device__ __forceinline__ Result sub_product(const SMEM& sm, int sa_sgn, int ea, bool a_zero,
                                               int sp_sgn, int ep, bool p_zero, uint32_t (&out)[M]) {
   constexpr int n = 32 * M;
   const int neg_p = sp_sgn ^ 1;  // a - P = a + (-P)
   if (p_zero) {
     // result is a itself (already normalised)
 #pragma unroll
-    for (int k = 0; k < M; ++k) out[k] = sm.sa[lane_id() * M + k];
+    for (int k = 0; k < M; ++k) out[k] = sm.sa[IX::at(lane_id() * M + k)];
     __syncwarp();
     Result r;
     r.zero = a_zero;
@@ -511,7 +538,7 @@ __device__ __forceinline__ Result sub_product(const WarpSmem<M>& sm, int sa_sgn,
       base = ep + o;
     }
   }
-  return combine<M>(X, sa_sgn, Y, neg_p, base, sm.sa, out);
+  return combine<M, IX>(X, sa_sgn, Y, neg_p, base, sm.sa, out);
 }
 
 }  // namespace hk
