@@ -10,7 +10,9 @@ libhk's CUDA kernels.  Workload: beta = 1/2, N = 1024, k = 32 at 24576 bits
 Output: one JSON line (rank 0).  value = solves/hour over all ranks (each rank
 solves its own instance: replicas, weak scaling), device time from CUDA events
 on the stream the library runs on.  roofline: the trailing-update kernel
-(Algorithm 1's inner loops) against the INT32 multiply-add (IMAD) pipe.
+(Algorithm 1's inner loops): executed modular multiplications of its NTT
+products against the INT32 multiply-add (IMAD) pipe, with the
+schoolbook-equivalent limb-product rate beside it.
 cpu_baseline: the CPU oracle timed on a bounded sample of the same workload.
 --impl reference: the oracle arm only (rank 0), same metric and config.
 """
@@ -33,6 +35,32 @@ UNIT = "solves/hour"
 # (mad.lo + mad.hi, with carry) per 32x32->64 limb product
 IMAD_PER_CLK_PER_SM = 64
 IMAD_PER_LIMB_MAC = 2
+# three IMAD-pipe instructions (mul.lo, mul.hi, mad) per modular multiplication
+# of the NTT product (Shoup's form; Montgomery's takes four)
+IMAD_PER_MODMUL = 3
+
+
+def ntt_shape(n):
+    """(rows, K) of the library's transform for n limbs: the least L = rows K
+    >= 2n with K a power of two and rows in {1, 3} (ties to rows = 1)."""
+    def log2c(x):
+        l = 0
+        while (1 << l) < x:
+            l += 1
+        return l
+    k3 = 1 << log2c((2 * n + 2) // 3)
+    k1 = 1 << log2c(2 * n)
+    return (3, k3) if 3 * k3 < k1 else (1, k1)
+
+
+def ntt_modmuls_per_update(n):
+    """Modular multiplications of one NTT product (three primes): pointwise
+    products, column three-point transforms, row butterflies, and Garner's
+    three per position; the forward transforms are shared by a whole step."""
+    rows, K = ntt_shape(n)
+    L = rows * K
+    per_prime = L + (K if rows == 3 else 0) + rows * (K // 2) * (K.bit_length() - 1)
+    return 3 * per_prime + 3 * L
 
 
 def parse():
@@ -223,19 +251,41 @@ def run_ours(a):
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak = sms * IMAD_PER_CLK_PER_SM / IMAD_PER_LIMB_MAC * sm_max * 1e6 / 1e12  # T limb-MAC/s
+    peak_sb = sms * IMAD_PER_CLK_PER_SM / IMAD_PER_LIMB_MAC * sm_max * 1e6 / 1e12  # T limb-MAC/s
     avg_launch_ms = prof["trailing_ms"] / max(prof["trailing_launches"], 1)
     macs_per_launch = prof["trailing_limb_macs"] / max(prof["trailing_launches"], 1)
-    achieved = macs_per_launch / (avg_launch_ms / 1e3) / 1e12
+    updates_per_launch = macs_per_launch / (n * n)
+    achieved_sb = macs_per_launch / (avg_launch_ms / 1e3) / 1e12
+    ntt = (a.bits // 1024) >= hk.HK_NTT_AUTO_MIN_M
     traffic = None
     tp = os.path.join(ROOT, "profiles", "trailing_traffic.json")
     if os.path.exists(tp):
         try:
             t = json.load(open(tp))
             if t.get("bits") == a.bits and t.get("kernel_source_sha") == kernel_sha():
-                traffic = t["bytes_per_limb_mac"] * macs_per_launch
+                traffic = t["bytes_per_update"] * updates_per_launch
         except (ValueError, KeyError):
             traffic = None
+    schoolbook = dict(achieved=achieved_sb, peak=peak_sb, unit="Tlimb-MAC/s", frac=achieved_sb / peak_sb,
+                      note=f"n^2 = {n * n} limb products per update (the schoolbook-equivalent convention); "
+                           f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_LIMB_MAC} IMAD per limb "
+                           f"product x {sm_max:.0f} MHz (derived)")
+    if ntt:
+        mm = ntt_modmuls_per_update(n)
+        peak = sms * IMAD_PER_CLK_PER_SM / IMAD_PER_MODMUL * sm_max * 1e6 / 1e12
+        achieved = mm * updates_per_launch / (avg_launch_ms / 1e3) / 1e12
+        roofline = dict(bound="alu", achieved=achieved, peak=peak, unit="Tmodmul/s", frac=achieved / peak,
+                        traffic=traffic, kernel="k_trailing_ntt (Algorithm 1 trailing update, NTT products)",
+                        work_per_update=f"{mm} modular multiplications (3 primes, length {ntt_shape(n)[0]} x "
+                                        f"{ntt_shape(n)[1]})",
+                        peak_note=f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_MODMUL} IMAD per "
+                                  f"modular multiplication x {sm_max:.0f} MHz (derived, not measured)",
+                        schoolbook_equiv=schoolbook)
+    else:
+        roofline = dict(bound="alu", achieved=achieved_sb, peak=peak_sb, unit="Tlimb-MAC/s",
+                        frac=achieved_sb / peak_sb, traffic=traffic,
+                        kernel="k_trailing (Algorithm 1 trailing update, schoolbook products)",
+                        peak_note=schoolbook["note"])
     d2h = ne * (8 + 4 * n) + min(ne, a.k - 1) * (8 + 4 * n) + (8 + 4 * n)
     lam_f64 = lam[3].tolist()
     out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=a.steps, warmup=a.warmup,
@@ -247,11 +297,7 @@ def run_ours(a):
                               f"{a.N * (a.N + 1) // 2 * (4 * n + 8) / 1e9:.2f} GB"),
                e2e=dict(value=e2e, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=d2h),
                gpu_launches=int(prof["launches"]),
-               roofline=dict(bound="alu", achieved=achieved, peak=peak, unit="Tlimb-MAC/s",
-                             frac=achieved / peak, traffic=traffic,
-                             kernel="k_trailing (Algorithm 1 trailing update)",
-                             peak_note=f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_LIMB_MAC} IMAD "
-                                       f"per limb product x {sm_max:.0f} MHz (derived, not measured)"),
+               roofline=roofline,
                phases_ms=dict(moments=prof["moments_ms"] / a.steps, ldlt=prof["ldlt_ms"] / a.steps,
                               trailing=prof["trailing_ms"] / a.steps, scale=prof["scale_ms"] / a.steps,
                               invblock=prof["invblock_ms"] / a.steps,
@@ -271,7 +317,7 @@ def kernel_sha():
     import hashlib
     hsh = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1810_01478_gb300", "csrc")
-    for f in ("mp_warp.cuh", "k_ldlt.cuh"):
+    for f in ("mp_warp.cuh", "ntt.cuh", "k_ldlt.cuh"):
         hsh.update(open(os.path.join(d, f), "rb").read())
     return hsh.hexdigest()[:16]
 

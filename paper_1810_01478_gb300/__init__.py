@@ -30,6 +30,7 @@ EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_
            "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run",
            "hk_set_product_algorithm"]
 HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT = 0, 1, 2
+HK_NTT_AUTO_MIN_M = 8  # include/hk.h: AUTO uses NTT products from 32 * 8 limbs (8192 bits)
 
 
 class Instance(ctypes.Structure):
