@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(128) k_alg4_step(MPVec A, MPVec X, int N, int 
 // Algorithm 4 step i with NTT products: FL[j - i - 1] = transform of L[j][i]
 // (unscaled), FXr[c] = transform of X[i][c] (scaled).
 template <int M>
-__global__ void __launch_bounds__(128) k_alg4_ntt(MPVec A, MPVec X, const uint32_t* __restrict__ FL,
+__global__ void __launch_bounds__(32 * HK_NTT_TRAIL_WARPS, 2) k_alg4_ntt(MPVec A, MPVec X, const uint32_t* __restrict__ FL,
                                                   const uint32_t* __restrict__ FXr, int N, int k, int i, NttConst nc) {
   constexpr int n = 32 * M;
   extern __shared__ uint32_t smem[];

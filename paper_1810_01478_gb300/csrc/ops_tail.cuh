@@ -164,11 +164,12 @@ struct Tail {
       const size_t per = (size_t)NTT_Q * nc.L;
       uint32_t* FL = c.ntt_buf;
       uint32_t* FXr = c.ntt_buf + per * N;
-      const size_t tsm = (size_t)W * NTT_Q * ntt_stride(nc.L) * 4, fsm = (size_t)W * ntt_stride(nc.L) * 4;
-      if ((st = check_cuda(c, allow_smem_blocks(k_alg4_ntt<M>, tsm, 2), "smem attribute")) ||
+      constexpr int NTW = Ops<M>::NTW;
+      const size_t tsm = (size_t)NTW * NTT_Q * ntt_stride(nc.L) * 4, fsm = (size_t)W * ntt_stride(nc.L) * 4;
+      if ((st = check_cuda(c, allow_smem(k_alg4_ntt<M>, tsm), "smem attribute")) ||
           (st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fsm), "smem attribute")))
         return st;
-      const int res = Ops<M>::resident_blocks(k_alg4_ntt<M>, 32 * W, tsm, c.device);
+      const int res = Ops<M>::resident_blocks(k_alg4_ntt<M>, 32 * NTW, tsm, c.device);
       const int fres = Ops<M>::resident_blocks(k_ntt_fwd<M>, 32 * W, fsm, c.device);
       for (int i = 0; i < N - 1; ++i) {
         const int cols = std::min(k, i);
@@ -182,8 +183,8 @@ struct Tail {
           k_ntt_fwd<M><<<g2, 32 * W, fsm, c.stream>>>(c.X.view(), (int64_t)i * k, cols, FXr, nc, 1);
           count_launch(c, 2);
         }
-        const int grid = (int)std::min<int64_t>((total + W - 1) / W, res);
-        k_alg4_ntt<M><<<grid, 32 * W, tsm, c.stream>>>(c.A.view(), c.X.view(), FL, FXr, N, k, i, nc);
+        const int grid = (int)std::min<int64_t>((total + NTW - 1) / NTW, res);
+        k_alg4_ntt<M><<<grid, 32 * NTW, tsm, c.stream>>>(c.A.view(), c.X.view(), FL, FXr, N, k, i, nc);
         count_launch(c);
       }
     } else {
