@@ -327,3 +327,61 @@ class Hankel:
 
     def export(self, what, first, count):
         return hk_export(self.ctx, what, first, count, self.n)
+
+
+# ---------------------------------------------------------------------------
+# differentiable front end
+# ---------------------------------------------------------------------------
+def _exact_beta(beta, max_den=1000):
+    """beta (a float, a 0-dim tensor or a Fraction) as an exact a/b with b <= max_den."""
+    from fractions import Fraction
+    v = Fraction(beta) if isinstance(beta, Fraction) else Fraction(float(beta))
+    r = v.limit_denominator(max_den)
+    if abs(float(r) - float(v)) > 2.0 ** -50 * abs(float(v)):
+        raise ValueError("beta must be a rational a/b with b <= %d" % max_den)
+    return r
+
+
+_LAMBDA1_FN = None
+
+
+def _torch_function():
+    global _LAMBDA1_FN
+    if _LAMBDA1_FN is not None:
+        return _LAMBDA1_FN
+    import torch
+
+    class Lambda1(torch.autograd.Function):
+        """lambda_1 of the k x k block of H_N^-1 as a float64 tensor of beta.
+
+        forward runs moments -> LDL^T -> Algorithm 4 -> block -> lambda_1 in
+        libhk at `bits` bits and also forms d lambda_1 / d beta (the adjoint
+        of hk_lambda1_grad, first-order perturbation of the block's top
+        eigenvalue); backward multiplies it by the incoming gradient.  beta
+        must be 1/m (moments exact on the device); the multiprecision values
+        stay available through Hankel."""
+
+        @staticmethod
+        def forward(ctx, beta, N, k, bits, device=0):
+            b = _exact_beta(beta.item() if hasattr(beta, "item") else beta)
+            with Hankel(device) as h:
+                h.moments(b.numerator, b.denominator, N, bits)
+                h.ldlt()
+                h.inv_block(k)
+                lam = h.lambda1(1)
+                g = h.lambda1_grad()
+            ctx.save_for_backward(torch.tensor(float(g[3][0]), dtype=torch.float64))
+            return torch.tensor(float(lam[3][0]), dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (g,) = ctx.saved_tensors
+            return grad_out * g.to(grad_out.device), None, None, None, None
+
+    _LAMBDA1_FN = Lambda1
+    return Lambda1
+
+
+def lambda1(beta, N, k, bits, device=0):
+    """Differentiable lambda_1(beta) (torch.autograd); see Lambda1 above."""
+    return _torch_function().apply(beta, N, k, bits, device)

@@ -256,10 +256,11 @@ __global__ void k_ntt_fwd(MPVec src, int64_t first, int count, uint32_t* __restr
 
 // trunc(a - x*y) with the product from stored transforms fx (unscaled) and fy
 // (scaled); nb: this warp's 3 ntt_stride(L) words of shared memory (reused for the combine).
-template <int M>
-__device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, const uint32_t* fx, bool x_zero, int sx,
-                                            int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
-                                            const uint32_t* amant, int sa_sgn, int ea, uint32_t (&out)[M]) {
+// stage_a(sa) writes the addend's n limbs into sa under IxPad.
+template <int M, class StageA>
+__device__ __forceinline__ Result fused_ntt_core(uint32_t* nb, const NttConst& nc, const uint32_t* fx, bool x_zero,
+                                                 int sx, int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
+                                                 StageA stage_a, int sa_sgn, int ea, uint32_t (&out)[M]) {
   constexpr int n = 32 * M;
   static_assert(WarpSmemPad<M>::words <= NTT_Q * ntt_stride(ntt_len(n)), "combine frame exceeds the NTT buffer");
   const bool p_zero = x_zero || y_zero;
@@ -270,10 +271,19 @@ __device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, co
   }
   WarpSmemPad<M> sm(nb);
   if (!p_zero) stage_product<M, IxPad>(sm.sp, lo, hi);
-  copy_to_smem<M, IxPad>(sm.sa, amant);
+  stage_a(sm.sa);
   __syncwarp();
   const bool a_zero = sm.sa[IxPad::at(n - 1)] == 0u;
   return sub_product<M, IxPad>(sm, sa_sgn, ea, a_zero, sx ^ sy, ex + ey, p_zero, out);
+}
+
+// the addend from global memory
+template <int M>
+__device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, const uint32_t* fx, bool x_zero, int sx,
+                                            int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
+                                            const uint32_t* amant, int sa_sgn, int ea, uint32_t (&out)[M]) {
+  return fused_ntt_core<M>(nb, nc, fx, x_zero, sx, ex, fy, y_zero, sy, ey,
+                           [&](uint32_t* sa) { copy_to_smem<M, IxPad>(sa, amant); }, sa_sgn, ea, out);
 }
 
 // The trailing update of step i with NTT products.  FU[c - i - 1], FB[r - i - 1]

@@ -86,6 +86,57 @@ __global__ void __launch_bounds__(128) k_chain(const ChainTask* __restrict__ tas
   }
 }
 
+// k_chain with NTT products: FX[i], FY[i] hold the transforms of X[i]
+// (unscaled) and Y[i] (scaled); the accumulator stays in registers.  Same
+// exact products and the same combine as k_chain, so the same results.
+template <int M>
+__global__ void __launch_bounds__(32 * HK_NTT_TRAIL_WARPS, 2)
+    k_chain_ntt(const ChainTask* __restrict__ tasks, int ntasks, MPVec X, MPVec Y, const uint32_t* __restrict__ FX,
+                const uint32_t* __restrict__ FY, MPVec INIT, MPVec OUT, NttConst nc) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * ntt_stride(nc.L);
+  const size_t per = (size_t)NTT_Q * nc.L;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int t = blockIdx.x * (blockDim.x >> 5) + wib; t < ntasks; t += nw) {
+    const ChainTask tk = tasks[t];
+    uint32_t acc[M];
+    int as = 0, ae = 0;
+    if (tk.flags & CH_ZERO_INIT) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) acc[k] = 0;
+    } else {
+      load_chunk<M>(INIT.mant + tk.init * n, acc);
+      as = INIT.sgn[tk.init] ^ ((tk.flags & CH_NEG_INIT) ? 1 : 0);
+      ae = INIT.exp[tk.init];
+    }
+    if (__shfl_sync(FULL, acc[M - 1], 31) == 0u) { as = 0; ae = 0; }
+    const int flip = (tk.flags & CH_ADD) ? 1 : 0;
+    for (int q = 0; q < tk.len; ++q) {
+      const int64_t ix = tk.x0 + (int64_t)q * tk.sx, iy = tk.y0 + (int64_t)q * tk.sy;
+      uint32_t o[M];
+      const Result r = fused_ntt_core<M>(
+          nb, nc, FX + (size_t)ix * per, X.mant[ix * n + n - 1] == 0u, X.sgn[ix], X.exp[ix], FY + (size_t)iy * per,
+          Y.mant[iy * n + n - 1] == 0u, Y.sgn[iy] ^ flip, Y.exp[iy],
+          [&](uint32_t* sa) {
+#pragma unroll
+            for (int k = 0; k < M; ++k) sa[IxPad::at(lane_id() * M + k)] = acc[k];
+          },
+          as, ae, o);
+#pragma unroll
+      for (int k = 0; k < M; ++k) acc[k] = o[k];
+      as = r.sgn;
+      ae = r.exp;
+      __syncwarp();
+    }
+    const bool zero = __shfl_sync(FULL, acc[M - 1], 31) == 0u;
+    Result r{zero ? 0 : (as ^ ((tk.flags & CH_NEG_OUT) ? 1 : 0)), zero ? 0 : ae, zero};
+    store_result<M>(OUT, tk.out, r, acc);
+    __syncwarp();
+  }
+}
+
 // Reciprocals of D[idx[i]] (or D[first + i] when idx == nullptr) into Rtab[i].
 template <int M>
 __global__ void k_recip_tab(MPVec D, const int64_t* __restrict__ idx, int64_t first, int count,

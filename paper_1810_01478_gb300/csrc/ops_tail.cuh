@@ -48,6 +48,38 @@ struct Tail {
     return check_cuda(c, cudaGetLastError(), "k_chain");
   }
 
+  // chains with NTT products: transforms of X[0, nx) and Y[0, ny) first
+  // (scratch from the stream-ordered pool), then k_chain_ntt.  Same results
+  // as chains().
+  static hk_status chains_ntt(Ctx& c, const std::vector<ChainTask>& t, MPVec X, int64_t nx, MPVec Y, int64_t ny,
+                              MPVec INIT, MPVec OUT) {
+    if (t.empty()) return HK_OK;
+    hk_status st = upload_tasks(c, t.data(), t.size() * sizeof(ChainTask));
+    if (st != HK_OK) return st;
+    const NttConst nc = ntt_const(n);
+    const size_t per = (size_t)NTT_Q * nc.L;
+    constexpr int NTW = Ops<M>::NTW;
+    const size_t fsm = (size_t)W * ntt_stride(nc.L) * 4, tsm = (size_t)NTW * NTT_Q * ntt_stride(nc.L) * 4;
+    if ((st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fsm), "smem attribute")) ||
+        (st = check_cuda(c, allow_smem(k_chain_ntt<M>, tsm), "smem attribute")))
+      return st;
+    uint32_t* F = nullptr;
+    if ((st = check_cuda(c, cudaMallocAsync(&F, (size_t)(nx + ny) * per * 4, c.stream), "chain transforms")) != HK_OK)
+      return st;
+    const int fres = Ops<M>::resident_blocks(k_ntt_fwd<M>, 32 * W, fsm, c.device);
+    k_ntt_fwd<M><<<(int)std::min<int64_t>((nx + W - 1) / W, fres), 32 * W, fsm, c.stream>>>(X, 0, (int)nx, F, nc, 0);
+    k_ntt_fwd<M><<<(int)std::min<int64_t>((ny + W - 1) / W, fres), 32 * W, fsm, c.stream>>>(Y, 0, (int)ny,
+                                                                                         F + nx * per, nc, 1);
+    const int res = Ops<M>::resident_blocks(k_chain_ntt<M>, 32 * NTW, tsm, c.device);
+    const int grid = (int)std::min<int64_t>(((int64_t)t.size() + NTW - 1) / NTW, res);
+    k_chain_ntt<M><<<grid, 32 * NTW, tsm, c.stream>>>(static_cast<const ChainTask*>(c.d_tasks), (int)t.size(), X, Y,
+                                                        F, F + nx * per, INIT, OUT, nc);
+    count_launch(c, 3);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(F, c.stream);
+    return check_cuda(c, e, "k_chain_ntt");
+  }
+
   static hk_status quots(Ctx& c, const std::vector<QuotTask>& t, MPVec A, MPVec D, const DevVec& R, MPVec OUT) {
     if (t.empty()) return HK_OK;
     hk_status st = upload_tasks(c, t.data(), t.size() * sizeof(QuotTask));
@@ -100,8 +132,12 @@ struct Tail {
 
   // dot products, split into chains of SEG terms whose partial sums are added
   // by a second level of chains (recursively).
-  static hk_status dots(Ctx& c, const std::vector<Dot>& d, MPVec X, MPVec Y, MPVec OUT, int level = 0) {
+  // nx, ny > 0: X and Y hold nx and ny numbers and the products go through
+  // transforms of them (NTT widths; worth it when every number is used often).
+  static hk_status dots(Ctx& c, const std::vector<Dot>& d, MPVec X, MPVec Y, MPVec OUT, int level = 0,
+                        int64_t nx = 0, int64_t ny = 0) {
     if (d.empty()) return HK_OK;
+    const bool ntt = nx > 0 && ny > 0 && use_ntt(M);
     int maxlen = 0;
     for (const Dot& e : d) maxlen = std::max(maxlen, e.len);
     if (maxlen <= SEG) {
@@ -110,7 +146,7 @@ struct Tail {
       for (const Dot& e : d)
         t.push_back(ChainTask{e.out, 0, e.x0, e.y0, e.sx, e.sy, e.len,
                               CH_ZERO_INIT | CH_ADD | (e.neg ? CH_NEG_OUT : 0)});
-      return chains(c, t, X, Y, X, OUT);
+      return ntt ? chains_ntt(c, t, X, nx, Y, ny, X, OUT) : chains(c, t, X, Y, X, OUT);
     }
     int64_t total = 0;
     for (const Dot& e : d) total += (e.len + SEG - 1) / SEG;
@@ -131,7 +167,7 @@ struct Tail {
       up.push_back(Dot{e.out, 0, base, 0, 1, segs, e.neg});
       base += segs;
     }
-    hk_status st = chains(c, t, X, Y, X, P->view());
+    hk_status st = ntt ? chains_ntt(c, t, X, nx, Y, ny, X, P->view()) : chains(c, t, X, Y, X, P->view());
     if (st != HK_OK) return st;
     return dots(c, up, ONE->view(), P->view(), OUT, level + 1);
   }
@@ -277,8 +313,9 @@ struct Tail {
     std::vector<Dot> sq;
     for (int a = 0; a < kk; ++a)
       for (int b = 0; b < kk; ++b) sq.push_back(Dot{(int64_t)a * k + b, (int64_t)a * k, b, 1, k, kk, false});
+    const int64_t kk2 = (int64_t)k * k;
     for (int it = 0; it < s0; ++it) {
-      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view())) != HK_OK) return st;
+      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view(), 0, kk2, kk2)) != HK_OK) return st;
       std::swap(*T0, *T1);
     }
     if ((st = rayleigh(c, Sm, T0->view(), k, kk, V, scal, slot)) != HK_OK) return st;
@@ -286,7 +323,7 @@ struct Tail {
     const int pslot = slot + 8;  // scal[pslot], scal[pslot + 1]: the next quotient
     int* flag = c.d_err + 8;
     for (int it = s0; it < 40; ++it) {
-      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view())) != HK_OK) return st;
+      if ((st = dots(c, sq, T0->view(), T0->view(), T1->view(), 0, kk2, kk2)) != HK_OK) return st;
       std::swap(*T0, *T1);
       if ((st = rayleigh(c, Sm, T0->view(), k, kk, V, scal, pslot)) != HK_OK) return st;
       // scal[pslot + 2] = nu' - 1 * nu

@@ -114,3 +114,28 @@ def test_schoolbook_and_ntt_factors_identical():
     finally:
         hk.hk_set_product_algorithm(hk.HK_PRODUCT_AUTO)
     assert digests[0] == digests[1]
+
+
+def test_schoolbook_and_ntt_paths_identical():
+    """Algorithm 4, the block, the eigen-solver (its matrix squarings run as
+    NTT chains at NTT widths) and the gradient give the same limbs with either
+    exact-product algorithm (N = 72, k = 16, 8192 bits)."""
+    import numpy as np
+    import paper_1810_01478_gb300 as hk
+    from tests.digest import x_digest
+    hk.load()
+    outs = []
+    try:
+        for alg in (hk.HK_PRODUCT_SCHOOLBOOK, hk.HK_PRODUCT_NTT):
+            hk.hk_set_product_algorithm(alg)
+            with hk.Hankel(0) as h:
+                h.moments(1, 2, 72, 8192)
+                h.ldlt()
+                h.inv_block(16)
+                lam = h.lambda1(3)
+                g = h.lambda1_grad()
+                outs.append((x_digest(h, hk, 72, 16), [np.asarray(a).tobytes() for a in lam[:3]],
+                             [np.asarray(a).tobytes() for a in g[:3]]))
+    finally:
+        hk.hk_set_product_algorithm(hk.HK_PRODUCT_AUTO)
+    assert outs[0] == outs[1]
