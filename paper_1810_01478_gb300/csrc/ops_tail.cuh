@@ -510,7 +510,7 @@ struct Tail {
       const int lo = std::max(0, s - N + 1), hi = std::min(s, N - 1);
       cd.push_back(Dot{s, lo, s - lo, 1, -1, hi - lo + 1, false});
     }
-    if ((st = dots(c, cd, y->view(), y->view(), cs->view())) != HK_OK) return st;
+    if ((st = dots(c, cd, y->view(), y->view(), cs->view(), 0, N, N)) != HK_OK) return st;
     // harmonic numbers H_t = sum_{j<=t} 1/j (Hillis-Steele scan of the reciprocals)
     {
       std::vector<int64_t> num(tmax + 1, 1), den(tmax + 1);
