@@ -151,14 +151,19 @@ struct Ops {
     }
     uint32_t* FU = c.ntt_buf;
     uint32_t* FB = c.ntt_buf ? c.ntt_buf + per * (size_t)N : nullptr;
+    // The launch that runs beside the next pivot's reciprocal (t0 > 0) leaves
+    // one block slot free: with every SM's registers taken by trailing blocks
+    // the reciprocal's warp could not start until the update had finished.
     auto trailing = [&](int i, int64_t t0, int64_t t1) {
       const int64_t cnt = t1 - t0;
       if (ntt) {
-        const int g = (int)std::min<int64_t>((cnt + NTW - 1) / NTW, ntt_res);
+        const int cap = (t0 > 0 && ntt_res > 1) ? ntt_res - 1 : ntt_res;
+        const int g = (int)std::min<int64_t>((cnt + NTW - 1) / NTW, cap);
         k_trailing_ntt<M><<<g, 32 * NTW, ntt_smem, c.stream>>>(c.A.view(), c.U.view(), FU, FB, N, i, t0, t1, nc,
                                                                    c.d_err);
       } else {
-        const int g = (int)std::min<int64_t>((cnt + WARPS - 1) / WARPS, trail_res);
+        const int cap = (t0 > 0 && trail_res > 1) ? trail_res - 1 : trail_res;
+        const int g = (int)std::min<int64_t>((cnt + WARPS - 1) / WARPS, cap);
         k_trailing<M><<<g, 32 * WARPS, fused_smem, c.stream>>>(c.A.view(), c.U.view(), N, i, t0, t1, c.d_err);
       }
     };
