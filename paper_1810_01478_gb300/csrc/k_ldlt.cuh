@@ -286,13 +286,102 @@ __device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, co
                            [&](uint32_t* sa) { copy_to_smem<M, IxPad>(sa, amant); }, sa_sgn, ea, out);
 }
 
-// The trailing update of step i with NTT products.  FU[c - i - 1], FB[r - i - 1]
-// hold the transforms of U[c] (unscaled) and B_i[r] (scaled) for this step.
 // Blocks of HK_NTT_TRAIL_WARPS warps, two resident per SM: at 768 limbs a warp
 // needs 19 KB of shared memory, so 2 x 6 warps fill the SM's 228 KB.
 #ifndef HK_NTT_TRAIL_WARPS
 #define HK_NTT_TRAIL_WARPS 6
 #endif
+
+// Column scale of step i with NTT products: U[r] = A[r][i] and
+// A[r][i] = B_i[r] = trunc(A[r][i] / d_i), the same exact quotient as k_scale
+// (warp_quot), with its two products A R and Q~ D from transforms.
+// FU[r - i - 1] = F(A[r][i]) (unscaled; the trailing update reuses it),
+// FRD = F(R) then F(D) (scaled), FQ[r - i - 1]: scratch for F(Q~) (the slot
+// that F(B_i[r]) takes afterwards).
+template <int M>
+__global__ void __launch_bounds__(32 * HK_NTT_TRAIL_WARPS, 2)
+    k_scale_ntt(MPVec A, MPVec U, int N, int i, const uint32_t* __restrict__ FU, const uint32_t* __restrict__ FRD,
+                uint32_t* FQ, const int* rec_meta, NttConst nc, int* err) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * ntt_stride(nc.L);
+  uint32_t* qs = nb + ntt_stride(nc.L) + 32;  // Q~ staged for its transform (nb[0, stride) is the work area)
+  if (*err & ERR_NOT_PD) return;
+  const size_t per = (size_t)NTT_Q * nc.L;
+  const int lane = lane_id();
+  const int64_t dpos = tri_pos(N, i, i);
+  uint32_t dc[M];
+  load_chunk<M>(A.mant + dpos * n, dc);
+  const int sh = rec_meta[0];
+  const int ed = A.exp[dpos];
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t r = i + 1 + (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; r < N; r += nw) {
+    const int64_t pos = tri_pos(N, r, i);
+    uint32_t ac[M], q[M];
+    load_chunk<M>(A.mant + pos * n, ac);
+    const int sa = A.sgn[pos], ea = A.exp[pos];
+    store_chunk<M>(U.mant + r * n, ac);
+    if (lane == 0) {
+      U.sgn[r] = sa;
+      U.exp[r] = ea;
+    }
+    const bool a_zero = __shfl_sync(FULL, ac[M - 1], 31) == 0u;
+    Result res;
+    if (a_zero) {
+#pragma unroll
+      for (int k = 0; k < M; ++k) q[k] = 0;
+      res = Result{0, 0, true};
+    } else {
+      const int t = (ncmp<M>(ac, dc) >= 0) ? n - 1 : n;
+      // Q~ = floor(A R / 2^shift), shift = 64n - 1 - 32t - sh
+      uint32_t plo[M], phi[M];
+      warp_mul_ntt<M>(FU + (size_t)(r - i - 1) * per, FRD, nb, nc, plo, phi);
+      __syncwarp();
+      const int shift = 64 * n - 1 - 32 * t - sh;
+#pragma unroll
+      for (int k = 0; k < M; ++k) {
+        nb[lane * M + k] = plo[k];
+        nb[n + lane * M + k] = phi[k];
+      }
+      if (lane == 0) nb[2 * n] = 0;
+      __syncwarp();
+      read_shifted<M>(nb, shift >> 5, shift & 31, q);
+      __syncwarp();
+      // Q~ D through F(Q~) (written and read back by this warp)
+#pragma unroll
+      for (int k = 0; k < M; ++k) qs[lane * M + k] = q[k];
+      __syncwarp();
+      uint32_t* fq = FQ + (size_t)(r - i - 1) * per;
+      warp_ntt_number<M>(qs, nb, fq, nc, false);
+      __syncwarp();
+      uint32_t qlo[M], qhi[M];
+      warp_mul_ntt<M, false>(fq, FRD + per, nb, nc, qlo, qhi);
+      __syncwarp();
+      quot_fix<M>(ac, dc, t, qlo, qhi, nb, q, err);
+      res = Result{sa, ea - ed - t, false};
+    }
+    store_result<M>(A, pos, res, q);
+    __syncwarp();
+  }
+}
+
+// Transforms (scaled) of the pivot's reciprocal R (n raw limbs) and of the
+// pivot D = A[dpos]: warp 0 and warp 1 of one block.
+template <int M>
+__global__ void k_ntt_pivot(const uint32_t* __restrict__ rec, MPVec A, int64_t dpos, uint32_t* __restrict__ FRD,
+                            NttConst nc) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  if (wib > 1) return;
+  uint32_t* buf = smem + wib * ntt_stride(nc.L);
+  warp_ntt_number<M>(wib == 0 ? rec : A.mant + dpos * n, buf, FRD + (size_t)wib * NTT_Q * nc.L, nc, true);
+}
+
+// The trailing update of step i with NTT products.  FU[c - i - 1], FB[r - i - 1]
+// hold the transforms of U[c] (unscaled) and B_i[r] (scaled) for this step.
+// Blocks of HK_NTT_TRAIL_WARPS warps (see k_scale_ntt above).
 template <int M>
 __global__ void __launch_bounds__(32 * HK_NTT_TRAIL_WARPS, 2) k_trailing_ntt(MPVec A, MPVec U, const uint32_t* __restrict__ FU,
                                                       const uint32_t* __restrict__ FB, int N, int i, int64_t t0,

@@ -215,6 +215,10 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
   __syncwarp();
 }
 
+template <int M>
+__device__ void quot_fix(const uint32_t (&a)[M], const uint32_t (&d)[M], int t, const uint32_t (&qlo)[M],
+                         const uint32_t (&qhi)[M], uint32_t* sp, uint32_t (&q)[M], int* err);
+
 // ---------------------------------------------------------------------------
 // exactly truncated quotient
 // ---------------------------------------------------------------------------
@@ -246,6 +250,17 @@ __device__ void warp_quot(const uint32_t (&a)[M], const uint32_t (&d)[M], const 
   __syncwarp();
   uint32_t qlo[M], qhi[M];
   warp_mul<M>(q, ys_tmp, sp, qlo, qhi);
+  quot_fix<M>(a, d, t, qlo, qhi, sp, q, err);
+}
+
+// The end of an exact quotient: given Q~ (q) and the product Q~ D as (qlo,
+// qhi), forms Rem = A 2^(32t) - Q~ D and steps Q~ up while Rem >= D.
+// sp: 2n words of scratch.
+template <int M>
+__device__ void quot_fix(const uint32_t (&a)[M], const uint32_t (&d)[M], int t, const uint32_t (&qlo)[M],
+                         const uint32_t (&qhi)[M], uint32_t* sp, uint32_t (&q)[M], int* err) {
+  constexpr int n = 32 * M;
+  const int lane = lane_id();
   // A * 2^(32t) as (lo, hi): stage A at limb offset t
 #pragma unroll
   for (int k = 0; k < M; ++k) {

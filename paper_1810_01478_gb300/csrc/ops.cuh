@@ -121,11 +121,11 @@ struct Ops {
     const bool ntt = use_ntt(M);
     NttConst nc{};
     size_t per = 0, ntt_smem = 0, fwd_smem = 0;
-    int ntt_res = 0, fwd_res = 0;
+    int ntt_res = 0, fwd_res = 0, scale_ntt_res = 0;
     if (ntt) {
       nc = ntt_const(n);
       per = (size_t)NTT_Q * nc.L;
-      const size_t need = 2 * per * (size_t)N;
+      const size_t need = 2 * per * (size_t)N + 2 * per;  // FU, FB, then F(R), F(D) of the current pivot
       if (c.ntt_cap < need) {
         if (c.ntt_buf) {
           cudaStreamSynchronize(c.stream);
@@ -148,9 +148,21 @@ struct Ops {
         return st;
       ntt_res = resident_blocks(k_trailing_ntt<M>, 32 * NTW, ntt_smem, c.device);
       fwd_res = resident_blocks(k_ntt_fwd<M>, 32 * WARPS, fwd_smem, c.device);
+      if ((st = check_cuda(c, allow_smem(k_scale_ntt<M>, ntt_smem), "smem attribute")) != HK_OK) return st;
+      scale_ntt_res = resident_blocks(k_scale_ntt<M>, 32 * NTW, ntt_smem, c.device);
     }
     uint32_t* FU = c.ntt_buf;
     uint32_t* FB = c.ntt_buf ? c.ntt_buf + per * (size_t)N : nullptr;
+    uint32_t* FRD = c.ntt_buf ? c.ntt_buf + 2 * per * (size_t)N : nullptr;
+    // the reciprocal of pivot i and, for NTT quotients, the transforms of R and d_i
+    auto pivot = [&](int i) {
+      k_recip_pivot<M><<<1, 32, recip_smem, c.aux>>>(c.A.view(), N, i, c.rec, c.rec_meta, c.d_err);
+      if (ntt) {
+        k_ntt_pivot<M><<<1, 64, 2 * ntt_stride(nc.L) * 4, c.aux>>>(c.rec, c.A.view(), tri_pos(N, i, i), FRD, nc);
+        count_launch(c);
+      }
+      cudaEventRecord(c.ev_recip, c.aux);
+    };
     // The launch that runs beside the next pivot's reciprocal (t0 > 0) leaves
     // one block slot free: with every SM's registers taken by trailing blocks
     // the reciprocal's warp could not start until the update had finished.
@@ -183,8 +195,7 @@ struct Ops {
     // reciprocal of d_0 on the auxiliary stream
     cudaEventRecord(c.ev_diag, s);
     cudaStreamWaitEvent(c.aux, c.ev_diag, 0);
-    k_recip_pivot<M><<<1, 32, recip_smem, c.aux>>>(c.A.view(), N, 0, c.rec, c.rec_meta, c.d_err);
-    cudaEventRecord(c.ev_recip, c.aux);
+    pivot(0);
     count_launch(c);
     for (int i = 0; i < N - 1; ++i) {
       const int64_t rows = N - 1 - i;
@@ -192,12 +203,18 @@ struct Ops {
       cudaStreamWaitEvent(s, c.ev_recip, 0);  // R_i is ready
       const int gs = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, scale_res);
       const size_t es = c.prof ? prof_mark(c) : 0;
-      k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(c.A.view(), c.U.view(), N, i, c.rec, c.rec_meta, c.d_err);
-      if (ntt) {  // transforms of U[i+1..N) and of B_i = A[i+1..N][i]
+      if (ntt) {
+        // F(U[r]) = F(A[r][i]) before the scale; the quotients A R and Q~ D
+        // through transforms; then F(B_i[r]) for the update
         const int g = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, fwd_res);
-        k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.U.view(), i + 1, (int)rows, FU, nc, 0);
+        k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FU, nc, 0);
+        const int gq = (int)std::min<int64_t>((rows + NTW - 1) / NTW, scale_ntt_res);
+        k_scale_ntt<M><<<gq, 32 * NTW, ntt_smem, s>>>(c.A.view(), c.U.view(), N, i, FU, FRD, FB, c.rec_meta, nc,
+                                                       c.d_err);
         k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FB, nc, 1);
         count_launch(c, 2);
+      } else {
+        k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(c.A.view(), c.U.view(), N, i, c.rec, c.rec_meta, c.d_err);
       }
       if (c.prof) c.scale_ev.push_back({es, prof_mark(c)});
       // look-ahead: update d_{i+1} = A[i+1][i+1] first (entry t = 0 of the trailing triangle) ...
@@ -210,8 +227,7 @@ struct Ops {
       // ... start its reciprocal on the auxiliary stream ...
       cudaEventRecord(c.ev_diag, s);
       cudaStreamWaitEvent(c.aux, c.ev_diag, 0);
-      k_recip_pivot<M><<<1, 32, recip_smem, c.aux>>>(c.A.view(), N, i + 1, c.rec, c.rec_meta, c.d_err);
-      cudaEventRecord(c.ev_recip, c.aux);
+      pivot(i + 1);
       // ... while the main stream updates the rest of the trailing triangle
       if (T > 1) {
         const size_t e1 = c.prof ? prof_mark(c) : 0;
