@@ -47,6 +47,17 @@ struct Ctx {
   // transforms of the current step's U and B columns (NTT products)
   uint32_t* ntt_buf = nullptr;
   size_t ntt_cap = 0;  // words
+  // Algorithm 4 beside the factorisation (NTT widths): the LDL^T runs on the
+  // high-priority stream `ms` (forked from and joined back to the caller's
+  // stream), marks each finished column i with ev_col[i], and hk_inv_block
+  // runs Algorithm 4's step i on the low-priority stream `a4` once column i
+  // is marked, with its own transform buffer ntt_buf2.
+  cudaStream_t ms = nullptr, a4 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_ldlt_start = nullptr, ev_a4 = nullptr;
+  std::vector<cudaEvent_t> ev_col;
+  bool cols_marked = false;
+  uint32_t* ntt_buf2 = nullptr;
+  size_t ntt_cap2 = 0;  // words
   // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
   std::map<std::string, DevVec> pool;
   void* d_tasks = nullptr;    // task descriptors of the current launch

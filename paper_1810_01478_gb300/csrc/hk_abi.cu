@@ -276,8 +276,14 @@ void hk_destroy(hk_ctx* h) {
   if (c.ev_diag) cudaEventDestroy(c.ev_diag);
   if (c.ev_recip) cudaEventDestroy(c.ev_recip);
   if (c.aux) cudaStreamDestroy(c.aux);
+  for (cudaEvent_t e : c.ev_col) cudaEventDestroy(e);
+  for (cudaEvent_t e : {c.ev_fork, c.ev_join, c.ev_ldlt_start, c.ev_a4})
+    if (e) cudaEventDestroy(e);
+  if (c.ms) cudaStreamDestroy(c.ms);
+  if (c.a4) cudaStreamDestroy(c.a4);
   if (c.rec) cudaFree(c.rec);
   if (c.ntt_buf) cudaFree(c.ntt_buf);
+  if (c.ntt_buf2) cudaFree(c.ntt_buf2);
   if (c.d_err) cudaFree(c.d_err);
   delete h;
 }

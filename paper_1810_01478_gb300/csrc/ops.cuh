@@ -94,8 +94,53 @@ struct Ops {
     return cudaGetLastError();
   }
 
-  // a2-a4: assemble H_N and run Algorithm 1 (Sec. 4.3) step by step.
+  // a2-a4: assemble H_N and run Algorithm 1 (Sec. 4.3) step by step.  At
+  // NTT widths the factorisation runs on the high-priority stream c.ms,
+  // forked from and joined back to the caller's stream, and marks every
+  // finished column for Algorithm 4 (see Ctx).
   static hk_status ldlt(Ctx& c) {
+    c.cols_marked = false;
+    if (!use_ntt(M)) return ldlt_body(c);
+    hk_status st;
+    if (!c.ms) {
+      int least = 0, greatest = 0;
+      cudaDeviceGetStreamPriorityRange(&least, &greatest);
+      if ((st = check_cuda(c, cudaStreamCreateWithPriority(&c.ms, cudaStreamNonBlocking, greatest), "stream")) ||
+          (st = check_cuda(c, cudaStreamCreateWithPriority(&c.a4, cudaStreamNonBlocking, least), "stream")))
+        return st;
+      for (cudaEvent_t* e : {&c.ev_fork, &c.ev_join, &c.ev_ldlt_start, &c.ev_a4})
+        if ((st = check_cuda(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming), "event")) != HK_OK) return st;
+    }
+    while ((int)c.ev_col.size() < c.N) {
+      cudaEvent_t e;
+      if ((st = check_cuda(c, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event")) != HK_OK) return st;
+      c.ev_col.push_back(e);
+    }
+    const size_t need2 = (size_t)NTT_Q * ntt_len(n) * ((size_t)c.N + 64);
+    if (c.ntt_cap2 < need2) {
+      if (c.ntt_buf2) {
+        cudaStreamSynchronize(c.stream);
+        cudaFree(c.ntt_buf2);
+        c.ntt_buf2 = nullptr;
+        c.ntt_cap2 = 0;
+      }
+      if ((st = check_cuda(c, cudaMalloc(&c.ntt_buf2, need2 * 4), "allocating the transforms")) != HK_OK) return st;
+      c.ntt_cap2 = need2;
+    }
+    cudaStream_t user = c.stream;
+    cudaEventRecord(c.ev_fork, user);
+    cudaEventRecord(c.ev_ldlt_start, user);
+    cudaStreamWaitEvent(c.ms, c.ev_fork, 0);
+    c.stream = c.ms;
+    st = ldlt_body(c);
+    c.stream = user;
+    cudaEventRecord(c.ev_join, c.ms);
+    cudaStreamWaitEvent(user, c.ev_join, 0);
+    if (st == HK_OK) c.cols_marked = true;
+    return st;
+  }
+
+  static hk_status ldlt_body(Ctx& c) {
     const int N = c.N;
     const int64_t tri = (int64_t)N * (N + 1) / 2;
     hk_status st;
@@ -181,7 +226,9 @@ struct Ops {
     };
     cudaStream_t s = c.stream;
     if (!c.aux) {
-      if ((st = check_cuda(c, cudaStreamCreateWithFlags(&c.aux, cudaStreamNonBlocking), "aux stream")) ||
+      int least = 0, greatest = 0;
+      cudaDeviceGetStreamPriorityRange(&least, &greatest);
+      if ((st = check_cuda(c, cudaStreamCreateWithPriority(&c.aux, cudaStreamNonBlocking, greatest), "aux stream")) ||
           (st = check_cuda(c, cudaEventCreateWithFlags(&c.ev_diag, cudaEventDisableTiming), "event")) ||
           (st = check_cuda(c, cudaEventCreateWithFlags(&c.ev_recip, cudaEventDisableTiming), "event")))
         return st;
@@ -213,6 +260,7 @@ struct Ops {
                                                        c.d_err);
         k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FB, nc, 1);
         count_launch(c, 2);
+        if (i < (int)c.ev_col.size()) cudaEventRecord(c.ev_col[i], s);  // column i of L is final
       } else {
         k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(c.A.view(), c.U.view(), N, i, c.rec, c.rec_meta, c.d_err);
       }

@@ -186,20 +186,27 @@ struct Tail {
       dev_free(c.S);
       if ((st = check_cuda(c, dev_alloc(c.S, (int64_t)k * k, n), "allocating S")) != HK_OK) return st;
     }
+    const bool ntt = use_ntt(M) && c.ntt_buf && c.ntt_cap >= 2 * (size_t)NTT_Q * ntt_len(n) * N;
+    // Algorithm 4 beside the factorisation: on the low-priority stream a4,
+    // step i after column i of L is marked (the LDL^T queued just before)
+    const bool beside = ntt && c.cols_marked && c.a4 && c.ntt_buf2 &&
+                        c.ntt_cap2 >= (size_t)NTT_Q * ntt_len(n) * ((size_t)N + k) && (int)c.ev_col.size() >= N;
+    c.cols_marked = false;
+    cudaStream_t xs = beside ? c.a4 : c.stream;
+    if (beside) cudaStreamWaitEvent(xs, c.ev_ldlt_start, 0);
     {
       const int64_t work = (int64_t)N * k * n;
       const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
-      k_x_init<M><<<grid, 256, 0, c.stream>>>(c.X.view(), N, k);
+      k_x_init<M><<<grid, 256, 0, xs>>>(c.X.view(), N, k);
       count_launch(c);
     }
-    const bool ntt = use_ntt(M) && c.ntt_buf && c.ntt_cap >= 2 * (size_t)NTT_Q * ntt_len(n) * N;
     if (ntt) {
       // Algorithm 4 with NTT products: per step, the transforms of the pivot
       // column L[i+1..N)[i] (unscaled) and of the finished row X[i][0..cols) (scaled)
       const NttConst nc = ntt_const(n);
       const size_t per = (size_t)NTT_Q * nc.L;
-      uint32_t* FL = c.ntt_buf;
-      uint32_t* FXr = c.ntt_buf + per * N;
+      uint32_t* FL = beside ? c.ntt_buf2 : c.ntt_buf;
+      uint32_t* FXr = FL + per * N;
       constexpr int NTW = Ops<M>::NTW;
       const size_t tsm = (size_t)NTW * NTT_Q * ntt_stride(nc.L) * 4, fsm = (size_t)W * ntt_stride(nc.L) * 4;
       if ((st = check_cuda(c, allow_smem(k_alg4_ntt<M>, tsm), "smem attribute")) ||
@@ -212,16 +219,23 @@ struct Tail {
         const int64_t per_row = cols + (i < k ? 1 : 0);
         const int64_t rows = N - 1 - i;
         const int64_t total = rows * per_row;
+        if (beside) cudaStreamWaitEvent(xs, c.ev_col[i], 0);
         if (cols > 0) {
           const int g1 = (int)std::min<int64_t>((rows + W - 1) / W, fres);
-          k_ntt_fwd<M><<<g1, 32 * W, fsm, c.stream>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FL, nc, 0);
+          k_ntt_fwd<M><<<g1, 32 * W, fsm, xs>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FL, nc, 0);
           const int g2 = (int)std::min<int64_t>((cols + W - 1) / W, fres);
-          k_ntt_fwd<M><<<g2, 32 * W, fsm, c.stream>>>(c.X.view(), (int64_t)i * k, cols, FXr, nc, 1);
+          k_ntt_fwd<M><<<g2, 32 * W, fsm, xs>>>(c.X.view(), (int64_t)i * k, cols, FXr, nc, 1);
           count_launch(c, 2);
         }
-        const int grid = (int)std::min<int64_t>((total + NTW - 1) / NTW, res);
-        k_alg4_ntt<M><<<grid, 32 * NTW, tsm, c.stream>>>(c.A.view(), c.X.view(), FL, FXr, N, k, i, nc);
+        // beside the factorisation: one update per warp, so that blocks are
+        // short and free their SM quickly for the higher-priority stream
+        const int grid = (int)std::min<int64_t>((total + NTW - 1) / NTW, beside ? (1 << 20) : res);
+        k_alg4_ntt<M><<<grid, 32 * NTW, tsm, xs>>>(c.A.view(), c.X.view(), FL, FXr, N, k, i, nc);
         count_launch(c);
+      }
+      if (beside) {
+        cudaEventRecord(c.ev_a4, xs);
+        cudaStreamWaitEvent(c.stream, c.ev_a4, 0);
       }
     } else {
       const size_t smem = Ops<M>::fused_smem;
