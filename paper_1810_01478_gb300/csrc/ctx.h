@@ -60,6 +60,8 @@ struct Ctx {
   size_t ntt_cap2 = 0;  // words
   // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
   std::map<std::string, DevVec> pool;
+  const uint32_t* one_mant = nullptr;  // pool "one" holds 1 while its mant is this (cleared on reallocation)
+  int one_n = 0;
   void* d_tasks = nullptr;    // task descriptors of the current launch
   size_t tasks_cap = 0;
   // profiling (hk_set_profiling): CUDA events around every trailing-update

@@ -160,6 +160,7 @@ DevVec* pool_get(Ctx& c, const std::string& name, int64_t count) {
   DevVec& v = c.pool[name];
   if (v.count >= count && v.n == c.n && v.mant) return &v;
   if (v.mant) cudaStreamSynchronize(c.stream);  // earlier kernels may still read it
+  if (v.mant && v.mant == c.one_mant) c.one_mant = nullptr;
   dev_free(v);
   if (dev_alloc(v, count, c.n) != cudaSuccess) {
     set_error(c, HK_ERR_NOMEM, "allocating scratch " + name);

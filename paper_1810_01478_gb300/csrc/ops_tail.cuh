@@ -123,10 +123,14 @@ struct Tail {
     return check_cuda(c, cudaGetLastError(), "k_small_ratio");
   }
 
-  // the constant 1 (pool "one")
+  // the constant 1 (pool "one"), formed once per allocation
   static DevVec* one(Ctx& c) {
     DevVec* v = pool_get(c, "one", 1);
-    if (v && small(c, {1}, {1}, v->view()) != HK_OK) return nullptr;
+    if (!v) return nullptr;
+    if (c.one_mant == v->mant && c.one_n == n) return v;
+    if (small(c, {1}, {1}, v->view()) != HK_OK) return nullptr;
+    c.one_mant = v->mant;
+    c.one_n = n;
     return v;
   }
 
@@ -164,12 +168,13 @@ struct Tail {
         t.push_back(ChainTask{base + g, 0, e.x0 + (int64_t)q0 * e.sx, e.y0 + (int64_t)q0 * e.sy, e.sx, e.sy, len,
                               CH_ZERO_INIT | CH_ADD});
       }
-      up.push_back(Dot{e.out, 0, base, 0, 1, segs, e.neg});
+      up.push_back(Dot{e.out, base, 0, 1, 0, segs, e.neg});  // P[base + q] * 1
       base += segs;
     }
     hk_status st = ntt ? chains_ntt(c, t, X, nx, Y, ny, X, P->view()) : chains(c, t, X, Y, X, P->view());
     if (st != HK_OK) return st;
-    return dots(c, up, ONE->view(), P->view(), OUT, level + 1);
+    // the constant 1 as the y operand: the schoolbook product skips its zero blocks
+    return dots(c, up, P->view(), ONE->view(), OUT, level + 1);
   }
 
   // ------------------------------------------------------------------------
@@ -341,7 +346,7 @@ struct Tail {
       std::swap(*T0, *T1);
       if ((st = rayleigh(c, Sm, T0->view(), k, kk, V, scal, pslot)) != HK_OK) return st;
       // scal[pslot + 2] = nu' - 1 * nu
-      if ((st = chains(c, {ChainTask{pslot + 2, pslot, 0, slot, 0, 0, 1, 0}}, ONE->view(), scal.view(),
+      if ((st = chains(c, {ChainTask{pslot + 2, pslot, slot, 0, 0, 0, 1, 0}}, scal.view(), ONE->view(),
                        scal.view(), scal.view())) != HK_OK)
         return st;
       k_rel_small<<<1, 32, 0, c.stream>>>(scal.view(), pslot + 2, scal.view(), pslot, n, tol, flag);
@@ -445,9 +450,9 @@ struct Tail {
       DevVec* ONE = one(c);
       if (!ONE) return c.sticky;
       std::vector<ChainTask> t;
-      for (int m = 0; m < ne1; ++m) t.push_back(ChainTask{m, m, 0, m, 0, 0, 1, 0});
-      // lam(k) - 1 * lam(k-1)
-      if ((st = chains(c, t, ONE->view(), LAM1->view(), LAM->view(), DIF->view())) != HK_OK) return st;
+      for (int m = 0; m < ne1; ++m) t.push_back(ChainTask{m, m, m, 0, 0, 0, 1, 0});
+      // lam(k) - lam(k-1) * 1
+      if ((st = chains(c, t, LAM1->view(), ONE->view(), LAM->view(), DIF->view())) != HK_OK) return st;
     }
     if ((st = read_device_flags(c)) != HK_OK) return st;
     c.n_eig = n_eig;
@@ -535,8 +540,8 @@ struct Tail {
         std::vector<ChainTask> t;
         t.reserve(tmax + 1);
         for (int64_t i = 0; i <= tmax; ++i)
-          t.push_back(i >= d ? ChainTask{i, i, 0, i - d, 0, 0, 1, CH_ADD} : ChainTask{i, i, 0, 0, 0, 0, 0, 0});
-        if ((st = chains(c, t, ONE->view(), H0->view(), H0->view(), H1->view())) != HK_OK) return st;
+          t.push_back(i >= d ? ChainTask{i, i, i - d, 0, 0, 0, 1, CH_ADD} : ChainTask{i, i, 0, 0, 0, 0, 0, 0});
+        if ((st = chains(c, t, H0->view(), ONE->view(), H0->view(), H1->view())) != HK_OK) return st;
         std::swap(*H0, *H1);
       }
     }
@@ -559,12 +564,12 @@ struct Tail {
     if ((st = small(c, kn, kd, kint->view())) != HK_OK) return st;
     std::vector<ChainTask> t1, t2, t3, t4;
     for (int s = 0; s <= 2 * N - 2; ++s) {
-      t1.push_back(ChainTask{s, m * (s + 1) - 1, 0, 1, 0, 0, 1, 0});             // H - 1*gamma
+      t1.push_back(ChainTask{s, m * (s + 1) - 1, 1, 0, 0, 0, 1, 0});             // H - gamma*1
       t2.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ADD});                      // 1 + kint*h
       t3.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ZERO_INIT | CH_ADD});       // mu*q
       t4.push_back(ChainTask{s, 0, 0, s, 0, 0, 1, CH_ZERO_INIT});                // -m*p
     }
-    if ((st = chains(c, t1, ONE->view(), cst->view(), H0->view(), hq->view())) != HK_OK) return st;
+    if ((st = chains(c, t1, cst->view(), ONE->view(), H0->view(), hq->view())) != HK_OK) return st;
     if ((st = chains(c, t2, kint->view(), hq->view(), ONE->view(), z->view())) != HK_OK) return st;
     if ((st = chains(c, t3, c.mu.view(), z->view(), z->view(), hq->view())) != HK_OK) return st;
     if ((st = chains(c, t4, cst->view(), hq->view(), hq->view(), z->view())) != HK_OK) return st;
