@@ -274,7 +274,8 @@ struct Tail {
     for (int a = 0; a < k; ++a)
       for (int b = a; b < k; ++b)
         dd.push_back(Dot{(int64_t)a * k + b, (int64_t)b * k + a, (int64_t)b * k + b, k, k, N - b, false});
-    if ((st = dots(c, dd, c.X.view(), Yq->view(), c.S.view())) != HK_OK) return st;
+    if ((st = dots(c, dd, c.X.view(), Yq->view(), c.S.view(), 0, (int64_t)N * k, (int64_t)N * k)) != HK_OK)
+      return st;
     std::vector<ChainTask> mirror;
     for (int a = 0; a < k; ++a)
       for (int b = a + 1; b < k; ++b)
