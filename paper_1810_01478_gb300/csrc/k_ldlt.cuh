@@ -256,8 +256,9 @@ __global__ void k_ntt_fwd(MPVec src, int64_t first, int count, uint32_t* __restr
 
 // trunc(a - x*y) with the product from stored transforms fx (unscaled) and fy
 // (scaled); nb: this warp's 3 ntt_stride(L) words of shared memory (reused for the combine).
-// stage_a(sa) writes the addend's n limbs into sa under IxPad.
-template <int M, class StageA>
+// stage_a(sa) writes the addend's n limbs into sa under IxPad.  X_RO: fx is
+// read-only for the kernel (see warp_mul_ntt).
+template <int M, class StageA, bool X_RO = true>
 __device__ __forceinline__ Result fused_ntt_core(uint32_t* nb, const NttConst& nc, const uint32_t* fx, bool x_zero,
                                                  int sx, int ex, const uint32_t* fy, bool y_zero, int sy, int ey,
                                                  StageA stage_a, int sa_sgn, int ea, uint32_t (&out)[M]) {
@@ -266,7 +267,7 @@ __device__ __forceinline__ Result fused_ntt_core(uint32_t* nb, const NttConst& n
   const bool p_zero = x_zero || y_zero;
   uint32_t lo[M], hi[M];
   if (!p_zero) {
-    warp_mul_ntt<M>(fx, fy, nb, nc, lo, hi);
+    warp_mul_ntt<M, X_RO>(fx, fy, nb, nc, lo, hi);
     __syncwarp();  // every lane has read the residues before the region is reused
   }
   WarpSmemPad<M> sm(nb);

@@ -315,6 +315,39 @@ __global__ void __launch_bounds__(128) k_backsub_step(MPVec A, MPVec Yv, int N, 
   }
 }
 
+// The same step with NTT products: FY = transform of y[j] (scaled); each
+// warp transforms its L[j][i] into its slot of FX (scratch, read back by the
+// same warp).
+template <int M>
+__global__ void __launch_bounds__(32 * HK_NTT_TRAIL_WARPS, 2)
+    k_backsub_ntt(MPVec A, MPVec Yv, int N, int j, const uint32_t* __restrict__ FY, uint32_t* FX, NttConst nc) {
+  constexpr int n = 32 * M;
+  extern __shared__ uint32_t smem[];
+  const int wib = threadIdx.x >> 5;
+  uint32_t* nb = smem + (size_t)wib * NTT_Q * ntt_stride(nc.L);
+  const size_t per = (size_t)NTT_Q * nc.L;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  uint32_t* fx = FX + (size_t)gw * per;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  const bool y_zero = Yv.mant[(int64_t)j * n + n - 1] == 0u;
+  for (int i = gw; i < j; i += nw) {
+    const int64_t lpos = tri_pos(N, j, i);
+    const bool x_zero = A.mant[lpos * n + n - 1] == 0u;
+    if (!x_zero && !y_zero) {
+      warp_ntt_number<M>(A.mant + lpos * n, nb, fx, nc, false);
+      __syncwarp();
+    }
+    uint32_t o[M];
+    const uint32_t* am = Yv.mant + (int64_t)i * n;
+    auto stage = [&](uint32_t* sa) { copy_to_smem<M, IxPad>(sa, am); };
+    const Result r = fused_ntt_core<M, decltype(stage), false>(nb, nc, fx, x_zero, A.sgn[lpos], A.exp[lpos], FY,
+                                                                y_zero, Yv.sgn[j], Yv.exp[j], stage, Yv.sgn[i],
+                                                                Yv.exp[i], o);
+    store_result<M>(Yv, i, r, o);
+    __syncwarp();
+  }
+}
+
 // Small exact constants: out[i] = trunc(num[i] / den[i]) for 64-bit integers
 // (num may be 0), formed by long division (one lane per number).
 template <int M>

@@ -513,7 +513,31 @@ struct Tail {
     for (int l = 0; l < N; ++l) qt.push_back(QuotTask{l, l, tri_pos(N, l, l), l, 0, 0});
     if ((st = quots(c, qt, z->view(), c.A.view(), *Rd, y->view())) != HK_OK) return st;
     // w = L^{-T} y by column back substitution
-    {
+    if (use_ntt(M)) {
+      // NTT products: per step the transform of y[j] (scaled), and each warp
+      // transforms its L[j][i] into its own scratch slot
+      const NttConst nc = ntt_const(n);
+      const size_t per = (size_t)NTT_Q * nc.L;
+      constexpr int NTW = Ops<M>::NTW;
+      const size_t fsm = (size_t)W * ntt_stride(nc.L) * 4, tsm = (size_t)NTW * NTT_Q * ntt_stride(nc.L) * 4;
+      if ((st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fsm), "smem attribute")) ||
+          (st = check_cuda(c, allow_smem(k_backsub_ntt<M>, tsm), "smem attribute")))
+        return st;
+      const int resb = Ops<M>::resident_blocks(k_backsub_ntt<M>, 32 * NTW, tsm, c.device);
+      uint32_t* F = nullptr;
+      if ((st = check_cuda(c, cudaMallocAsync(&F, ((size_t)resb * NTW + 1) * per * 4, c.stream), "transforms")) !=
+          HK_OK)
+        return st;
+      for (int j = N - 1; j >= 1; --j) {
+        k_ntt_fwd<M><<<1, 32, fsm, c.stream>>>(y->view(), j, 1, F, nc, 1);
+        const int grid = std::min((j + NTW - 1) / NTW, resb);
+        k_backsub_ntt<M><<<grid, 32 * NTW, tsm, c.stream>>>(c.A.view(), y->view(), N, j, F, F + per, nc);
+        count_launch(c, 2);
+      }
+      const cudaError_t e = cudaGetLastError();
+      cudaFreeAsync(F, c.stream);
+      if ((st = check_cuda(c, e, "back substitution")) != HK_OK) return st;
+    } else {
       const size_t smem = Ops<M>::fused_smem;
       if ((st = check_cuda(c, allow_smem(k_backsub_step<M>, smem), "smem attribute")) != HK_OK) return st;
       const int resb = Ops<M>::resident_blocks(k_backsub_step<M>, 32 * W, smem, c.device);
