@@ -123,15 +123,15 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
     __syncwarp();
   }
   // initial approximation from the top 64 bits, from below:
-  // R0_top <= 2^126 / (D_hi + 1) and R0 = R0_top * 2^(32n-63)
+  // R0_top = floor(2^126 / (D_hi + 1)) (exact integer division, about 61
+  // correct bits) and R0 = R0_top * 2^(32n-63)
   {
     const uint32_t h1 = __shfl_sync(FULL, dp[M - 1], 31);
     uint32_t h0b;
     if constexpr (M >= 2) h0b = __shfl_sync(FULL, dp[M - 2], 31);
     else h0b = __shfl_sync(FULL, dp[0], 30);
     const uint64_t Dhi = ((uint64_t)h1 << 32) | h0b;
-    const double t = ldexp(1.0, 126) / ((double)Dhi * (1.0 + ldexp(1.0, -40)));
-    const uint64_t r0 = ((uint64_t)t) << 1;  // R0_top * 2
+    const uint64_t r0 = (uint64_t)(((u128)1 << 126) / ((u128)Dhi + 1)) << 1;  // R0_top * 2
 #pragma unroll
     for (int k = 0; k < M; ++k) {
       const int i = lane * M + k;
@@ -149,9 +149,11 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
   // The precision doubles per step, so R is kept truncated to its top w limbs
   // (w = 4, 8, 16, ... limbs; truncation keeps R below the true value) and the
   // two products skip R's zero limbs (warp_mul skips all-zero blocks of y).
-  // `bits` is a lower bound on R's correct bits: 40 from the double start,
-  // doubling per step while below the truncation width (32 w - 8).
-  int w = 2, bits = 40;
+  // `bits` is a lower bound on R's correct bits: 60 from the start above,
+  // doubling per step while below the truncation width (32 w - 8); with 60
+  // the schedule w = 4, 8, ..., 512 reaches 32n - 8 bits at w = n = 768 in a
+  // single full-width step.
+  int w = 2, bits = 60;
 #pragma unroll 1
   for (int it = 0; it < 48; ++it) {
     w = min(n, 2 * w);
