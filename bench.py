@@ -177,6 +177,23 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(values, device):
+    """Element-wise maximum over all ranks (the slowest rank's times); the
+    values themselves with one rank."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def solves_per_hour(steps, world_size, ms):
+    """Whole-job throughput: every rank solves `steps` instances (replicas)
+    within the slowest rank's `ms`."""
+    return 3600.0 * steps * world_size / (ms / 1e3)
+
+
 def run_reference(a):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -241,13 +258,9 @@ def run_ours(a):
     clk = clocks.stop()
     prof = hk.hk_get_profile(h.ctx)
     dev_ms = ev0.elapsed_time(ev1)
-    times = torch.tensor([dev_ms, wall * 1e3], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(times, op=torch.distributed.ReduceOp.MAX)
-    dev_ms, wall_ms = times.tolist()
-    solves = a.steps * ws
-    value = 3600.0 * solves / (dev_ms / 1e3)
-    e2e = 3600.0 * solves / (wall_ms / 1e3)
+    dev_ms, wall_ms = reduce_max([dev_ms, wall * 1e3], "cuda")
+    value = solves_per_hour(a.steps, ws, dev_ms)
+    e2e = solves_per_hour(a.steps, ws, wall_ms)
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
