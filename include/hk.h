@@ -91,8 +91,27 @@ HK_API const char* hk_last_error(const hk_ctx* ctx);
  * build computes them on the device for beta = 1/m (m >= 1 an integer), where
  * they are the integers m * (m(j+1)-1)!  (beta = 1/2: 2 (2j+1)!; beta = 1: j!),
  * formed exactly and truncated once.  Any other beta returns
- * HK_ERR_UNSUPPORTED: import the moments with hk_set_moments instead. */
+ * HK_ERR_UNSUPPORTED: use hk_moments_gamma (constants Gamma(r/a) supplied)
+ * or import the moments with hk_set_moments. */
 HK_API hk_status hk_moments(hk_ctx* ctx, int64_t beta_num, int64_t beta_den, int N, int bits);
+
+/* a1 for a rational beta = beta_num/beta_den = a/b (lowest terms, a <= 64)
+ * from supplied constants C_r = Gamma(r/a), r = 1..a-1 (Sec. 2, eq.
+ * "moments"): with b(j+1) = q a + r, 0 <= r < a, the functional equation
+ * Gamma(x+1) = x Gamma(x) gives mu_j = b C_r prod_{i<q} (r + i a) / a^(q+1),
+ * and mu_j = b (q-1)! / a when r = 0.  Each mu_j is that exact product of the
+ * given constant (a binary number) with a rational, truncated once to `bits`.
+ *   nc:      limbs per constant
+ *   c_exp:   host, a-1 limb exponents (C_r = M_r 2^(32 c_exp[r-1]))
+ *   c_limbs: host, (a-1) x nc limbs, M_r little endian, top limb non-zero
+ * The constants should carry at least bits + 128 correct bits (the result is
+ * the exact truncation of the product with the constants as given; a moment
+ * with fewer than bits/32 limbs of constant-derived value sets HK_ERR_ARG at
+ * the next synchronising call).  a = 1 (beta = 1/m) needs no constants and
+ * behaves as hk_moments.  b (2N-1) < 2^31.  The constants are copied before
+ * the call returns. */
+HK_API hk_status hk_moments_gamma(hk_ctx* ctx, int64_t beta_num, int64_t beta_den, int N, int bits, int nc,
+                                  const int32_t* c_exp, const uint32_t* c_limbs);
 
 /* a1'. Import 2N-1 moments (host arrays, number layout above) for any weight;
  * beta_num/beta_den is recorded for hk_lambda1_grad (0/0 = unknown). */
@@ -191,6 +210,9 @@ typedef struct hk_instance {
   const int32_t* mu_sign;       /* host, 2N-1 moments, or NULL */
   const int32_t* mu_exp;
   const uint32_t* mu_limbs;
+  const int32_t* gamma_exp;     /* host, constants of hk_moments_gamma (a-1 of */
+  const uint32_t* gamma_limbs;  /* gamma_nc limbs), used when mu_* are NULL and */
+                                /* beta is not 1/m; else NULL */
   int32_t* lambda_sign;         /* host outputs, n_eig numbers, or NULL */
   int32_t* lambda_exp;
   uint32_t* lambda_limbs;
@@ -198,7 +220,7 @@ typedef struct hk_instance {
   double trunc_err_f64[3];
   double seconds;               /* wall time of this instance */
   int32_t status;
-  int32_t reserved;
+  int32_t gamma_nc;
   char message[128];            /* hk_last_error of a failed instance ("" if none) */
 } hk_instance;
 HK_API hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_concurrent);

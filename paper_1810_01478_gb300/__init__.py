@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
            "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
            "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run",
-           "hk_set_product_algorithm"]
+           "hk_set_product_algorithm", "hk_moments_gamma"]
 HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT = 0, 1, 2
 HK_NTT_AUTO_MIN_M = 8  # include/hk.h: AUTO uses NTT products from 32 * 8 limbs (8192 bits)
 
@@ -38,9 +38,10 @@ class Instance(ctypes.Structure):
     _fields_ = [("beta_num", ctypes.c_int64), ("beta_den", ctypes.c_int64), ("N", ctypes.c_int32),
                 ("k", ctypes.c_int32), ("bits", ctypes.c_int32), ("n_eig", ctypes.c_int32),
                 ("mu_sign", ctypes.c_void_p), ("mu_exp", ctypes.c_void_p), ("mu_limbs", ctypes.c_void_p),
+                ("gamma_exp", ctypes.c_void_p), ("gamma_limbs", ctypes.c_void_p),
                 ("lambda_sign", ctypes.c_void_p), ("lambda_exp", ctypes.c_void_p), ("lambda_limbs", ctypes.c_void_p),
                 ("lambda_f64", ctypes.c_double * 3), ("trunc_err_f64", ctypes.c_double * 3),
-                ("seconds", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int32), ("gamma_nc", ctypes.c_int32),
                 ("message", ctypes.c_char * 128)]
 PROFILE_FIELDS = 10
 
@@ -76,6 +77,8 @@ def load(path=LIB_PATH):
     L.hk_moments.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int]
     L.hk_set_moments.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I32P, _I32P, _U32P, ctypes.c_int64,
                                  ctypes.c_int64]
+    L.hk_moments_gamma.argtypes = [_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   _I32P, _U32P]
     L.hk_ldlt.argtypes = [_P]
     L.hk_inv_block.argtypes = [_P, ctypes.c_int]
     L.hk_lambda1.argtypes = [_P, ctypes.c_int, _I32P, _I32P, _U32P, _F64P, _F64P]
@@ -89,7 +92,7 @@ def load(path=LIB_PATH):
     L.hk_ldlt_noalloc.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 6 + [_P]
     L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
     for name in ("hk_set_product_algorithm", "hk_batch_run", "hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
-                 "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch"):
+                 "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch", "hk_moments_gamma"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -131,6 +134,16 @@ def hk_last_error(ctx):
 
 def hk_moments(ctx, beta_num, beta_den, N, bits):
     _check(load().hk_moments(ctx, beta_num, beta_den, N, bits), ctx)
+
+
+def hk_moments_gamma(ctx, beta_num, beta_den, N, bits, c_exp, c_limbs):
+    """Moments for beta = a/b from constants Gamma(r/a), r = 1..a-1:
+    c_exp (a-1 int32 limb exponents), c_limbs ((a-1) x nc uint32)."""
+    c_exp = np.ascontiguousarray(c_exp, dtype=np.int32)
+    c_limbs = np.ascontiguousarray(c_limbs, dtype=np.uint32)
+    nc = c_limbs.shape[1] if c_limbs.ndim == 2 and c_limbs.shape[0] else 1
+    _check(load().hk_moments_gamma(ctx, beta_num, beta_den, N, bits, nc, _ptr(c_exp, ctypes.c_int32),
+                                   _ptr(c_limbs, ctypes.c_uint32)), ctx)
 
 
 def hk_set_moments(ctx, N, bits, sign, exp, limbs, beta_num=0, beta_den=0):
@@ -225,11 +238,12 @@ def hk_ldlt_noalloc(bits, N, mu, factor, stream=None):
 
 def hk_batch_run(device, problems, max_concurrent=0):
     """Solve several instances concurrently.  problems: list of dicts with
-    beta (num, den), N, k, bits, n_eig and optional mu = (sign, exp, limbs)
-    host arrays.  Returns a list of dicts (status, lambda_f64, trunc_err_f64,
-    lambda = (sign, exp, limbs), seconds) in the same order."""
+    beta (num, den), N, k, bits, n_eig and optionally mu = (sign, exp, limbs)
+    (imported moments) or gamma = (exp, limbs) (the constants of
+    hk_moments_gamma).  Returns a list of dicts (status, lambda_f64,
+    trunc_err_f64, lambda = (sign, exp, limbs), seconds) in the same order."""
     arr = (Instance * len(problems))()
-    keep = []
+    keep, lams = [], []
     for i, p in enumerate(problems):
         it = arr[i]
         it.beta_num, it.beta_den = p["beta"]
@@ -240,25 +254,23 @@ def hk_batch_run(device, problems, max_concurrent=0):
                        np.ascontiguousarray(p["mu"][2], np.uint32))
             keep += [s, e, m]
             it.mu_sign, it.mu_exp, it.mu_limbs = s.ctypes.data, e.ctypes.data, m.ctypes.data
+        if p.get("gamma") is not None:
+            ge = np.ascontiguousarray(p["gamma"][0], np.int32)
+            gl = np.ascontiguousarray(p["gamma"][1], np.uint32)
+            keep += [ge, gl]
+            it.gamma_exp, it.gamma_limbs, it.gamma_nc = ge.ctypes.data, gl.ctypes.data, gl.shape[1]
         ls = np.zeros(it.n_eig, np.int32)
         le = np.zeros(it.n_eig, np.int32)
         lm = np.zeros((it.n_eig, n), np.uint32)
-        keep += [ls, le, lm]
+        lams.append((ls, le, lm))
         it.lambda_sign, it.lambda_exp, it.lambda_limbs = ls.ctypes.data, le.ctypes.data, lm.ctypes.data
     st = load().hk_batch_run(device, arr, len(problems), max_concurrent)
     out = []
     for i in range(len(problems)):
         it = arr[i]
-        out.append(dict(status=it.status, message=it.message.decode(errors="replace"),
-                        lambda_f64=list(it.lambda_f64)[:it.n_eig],
-                        trunc_err_f64=list(it.trunc_err_f64)[:it.n_eig], seconds=it.seconds))
-    # lambda arrays in problem order (the last three kept arrays of each problem)
-    j = 0
-    for i, p in enumerate(problems):
-        if p.get("mu") is not None:
-            j += 3
-        out[i]["lambda"] = (keep[j], keep[j + 1], keep[j + 2])
-        j += 3
+        out.append({"status": it.status, "message": it.message.decode(errors="replace"),
+                    "lambda_f64": list(it.lambda_f64)[:it.n_eig],
+                    "trunc_err_f64": list(it.trunc_err_f64)[:it.n_eig], "seconds": it.seconds, "lambda": lams[i]})
     return st, out
 
 
@@ -308,6 +320,10 @@ class Hankel:
     def moments(self, beta_num, beta_den, N, bits):
         self.n = bits // 32
         hk_moments(self.ctx, beta_num, beta_den, N, bits)
+
+    def moments_gamma(self, beta_num, beta_den, N, bits, c_exp, c_limbs):
+        self.n = bits // 32
+        hk_moments_gamma(self.ctx, beta_num, beta_den, N, bits, c_exp, c_limbs)
 
     def set_moments(self, N, bits, sign, exp, limbs, beta_num=0, beta_den=0):
         self.n = bits // 32

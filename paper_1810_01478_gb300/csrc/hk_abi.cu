@@ -343,6 +343,62 @@ hk_status hk_moments(hk_ctx* h, int64_t beta_num, int64_t beta_den, int N, int b
   return HK_OK;
 }
 
+hk_status hk_moments_gamma(hk_ctx* h, int64_t beta_num, int64_t beta_den, int N, int bits, int nc,
+                           const int32_t* c_exp, const uint32_t* c_limbs) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (beta_num <= 0 || beta_den <= 0) return set_error(c, HK_ERR_ARG, "beta must be positive");
+  int64_t x = beta_num, y = beta_den;
+  while (y) {
+    const int64_t t = x % y;
+    x = y;
+    y = t;
+  }
+  const int64_t a = beta_num / x, b = beta_den / x;
+  if (a == 1) return hk_moments(h, beta_num, beta_den, N, bits);
+  if (a > 64) return set_error(c, HK_ERR_UNSUPPORTED, "beta = a/b with a > 64");
+  if (nc < 1 || nc > 4096 || !c_exp || !c_limbs) return set_error(c, HK_ERR_ARG, "need a-1 constants of nc limbs");
+  if (N < 1 || b * (2 * (int64_t)N - 1) >= (1ll << 31)) return set_error(c, HK_ERR_ARG, "b (2N-1) too large");
+  for (int64_t r = 1; r < a; ++r)
+    if (c_limbs[(r - 1) * nc + nc - 1] == 0u) return set_error(c, HK_ERR_ARG, "constants must be normalised");
+  if ((st = begin_moments(h, N, bits)) != HK_OK) return st;
+  // bits of G for the largest moment: 2^64 b M_r prod_{i<q} (r + i a), q = b(2N-1)/a
+  const double q = (double)b * (2.0 * N - 1.0) / (double)a;
+  const double gbits = 64.0 + std::log2((double)b) + 32.0 * nc + q * std::log2((double)a) +
+                       (std::lgamma(q + 2.0)) / std::log(2.0) + 64.0;
+  const int64_t cap = ((int64_t)(gbits / 32.0) + 2 + 31) / 32 * 32;
+  constexpr int kWarps = 8;
+  if (cap * 4 * kWarps > 200 * 1024) return set_error(c, HK_ERR_UNSUPPORTED, "moments too long for the kernel");
+  int32_t* d_exp = nullptr;
+  uint32_t* d_lim = nullptr;
+  if ((st = check_cuda(c, cudaMallocAsync(&d_exp, (size_t)(a - 1) * 4, c.stream), "constants")) ||
+      (st = check_cuda(c, cudaMallocAsync(&d_lim, (size_t)(a - 1) * nc * 4, c.stream), "constants")) ||
+      (st = check_cuda(c, cudaMemcpyAsync(d_exp, c_exp, (size_t)(a - 1) * 4, cudaMemcpyHostToDevice, c.stream),
+                       "constants H2D")) ||
+      (st = check_cuda(c, cudaMemcpyAsync(d_lim, c_limbs, (size_t)(a - 1) * nc * 4, cudaMemcpyHostToDevice,
+                                          c.stream), "constants H2D")) ||
+      (st = check_cuda(c, cudaStreamSynchronize(c.stream), "constants H2D")))
+    return st;
+  if ((st = check_cuda(c, cudaFuncSetAttribute(k_moments_gamma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               200 * 1024), "smem attribute")) != HK_OK)
+    return st;
+  const size_t pe0 = c.prof ? prof_mark(c) : 0;
+  const int blocks = (2 * N - 1 + kWarps - 1) / kWarps;
+  k_moments_gamma<<<blocks, 32 * kWarps, (size_t)cap * 4 * kWarps, c.stream>>>((int)a, (int)b, N, c.n, (int)cap,
+                                                                               nc, d_exp, d_lim, c.mu.view(),
+                                                                               c.d_err);
+  count_launch(c);
+  if (c.prof) c.stage_ev.push_back({0, {pe0, prof_mark(c)}});
+  cudaFreeAsync(d_exp, c.stream);
+  cudaFreeAsync(d_lim, c.stream);
+  if ((st = check_cuda(c, cudaGetLastError(), "launching the moments")) != HK_OK) return st;
+  c.beta_num = beta_num;
+  c.beta_den = beta_den;
+  c.stage = ST_MOMENTS;
+  return HK_OK;
+}
+
 hk_status hk_set_moments(hk_ctx* h, int N, int bits, const int32_t* sign, const int32_t* exp,
                          const uint32_t* limbs, int64_t beta_num, int64_t beta_den) {
   hk_status st = enter(h);
@@ -529,6 +585,8 @@ static void run_instance(int device, hk_instance& in) {
   if (st == HK_OK) {
     if (in.mu_sign && in.mu_exp && in.mu_limbs)
       st = hk_set_moments(h, in.N, in.bits, in.mu_sign, in.mu_exp, in.mu_limbs, in.beta_num, in.beta_den);
+    else if (in.gamma_exp && in.gamma_limbs && in.gamma_nc > 0)
+      st = hk_moments_gamma(h, in.beta_num, in.beta_den, in.N, in.bits, in.gamma_nc, in.gamma_exp, in.gamma_limbs);
     else
       st = hk_moments(h, in.beta_num, in.beta_den, in.N, in.bits);
   }

@@ -2,8 +2,10 @@
 concurrently, beta in {9/20, 1/2, 11/20, 1} x N in {128, 192, 256, 384},
 k = 16, 32 N bits each.  Every instance must give exactly the lambda of the
 plain single-instance path (same kernels, bit for bit) and match the oracle
-to 1e-40.  Moments: on the device for beta = 1/2 and 1; for 9/20 and 11/20
-formed by the oracle from its stored Gamma(r/a) constants and imported.
+to 1e-40.  Moments: on the device; for 9/20 and 11/20 from the constants
+Gamma(r/a) (hk_moments_gamma), the oracle's own stored constants, and the
+single-instance path imports the oracle's moments formed from them (so the
+two routes to the moments are compared too).
 """
 import json
 import os
@@ -15,6 +17,7 @@ mpm = pytest.importorskip("mpmath")
 
 from oracle import mpfloat as F
 from tests.layout import to_arrays
+from tests.test_gpu_moments_gamma import as_limbs
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -39,15 +42,17 @@ def problems(ns=NS, betas=BETAS):
             p = dict(beta=(a, b), N=N, k=16, bits=bits, n_eig=1)
             if a != 1:
                 beta = Fraction(a, b)
-                p["mu"] = to_arrays(OM.moments_from_constants(beta, N, bits // 32, constants(beta)), bits // 32)
+                p["gamma"] = as_limbs(constants(beta))
+                p["mu_oracle"] = to_arrays(OM.moments_from_constants(beta, N, bits // 32, constants(beta)),
+                                           bits // 32)
             out.append(p)
     return out
 
 
 def single(hk, p):
     with hk.Hankel(0) as h:
-        if "mu" in p:
-            h.set_moments(p["N"], p["bits"], *p["mu"], p["beta"][0], p["beta"][1])
+        if "mu_oracle" in p:
+            h.set_moments(p["N"], p["bits"], *p["mu_oracle"], p["beta"][0], p["beta"][1])
         else:
             h.moments(p["beta"][0], p["beta"][1], p["N"], p["bits"])
         h.ldlt()
