@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="only run moments + LDL^T once at --N/--bits (a small case for ncu captures)")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="batch: 16 uneven instances (beta = 1/m, m in 1..4, N in {128..384}, k = 16, "
+                         "32 N bits) through hk_batch_run, beside the same instances one by one")
     return ap.parse_args()
 
 
@@ -346,9 +349,58 @@ def profile_case(a):
     print("profile case done", a.N, a.bits)
 
 
+def run_batch(a):
+    """The batched form: 16 instances of uneven size in one hk_batch_run (one
+    context, stream and host thread each), timed beside the same instances
+    solved one after another on one stream.  beta = 1/m (moments exact on the
+    device) with m in {1, 2, 3, 4}, N in {128, 192, 256, 384}, k = 16,
+    32 N bits: the shapes of the paper-scale batched configuration."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1810_01478_gb300 as hk
+    probs = [dict(beta=(1, m), N=N, k=16, bits=32 * N, n_eig=1) for m in (1, 2, 3, 4) for N in (128, 192, 256, 384)]
+
+    def batched():
+        st, res = hk.hk_batch_run(0, probs, max_concurrent=len(probs))
+        assert st == hk.HK_OK, [r["message"] for r in res if r["status"]]
+        return res
+
+    def sequential():
+        out = []
+        for p in probs:
+            with hk.Hankel(0) as h:
+                h.moments(*p["beta"], p["N"], p["bits"])
+                h.ldlt()
+                h.inv_block(p["k"])
+                out.append(h.lambda1(1))
+        return out
+
+    for _ in range(max(1, a.warmup)):
+        batched()
+    torch.cuda.synchronize()
+    times = {}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            fn()
+        torch.cuda.synchronize()
+        times[name] = (time.perf_counter() - t0) / a.steps
+    per_hour = 3600.0 * len(probs) / times["batched"]
+    print(json.dumps(dict(metric="instances/hour (16 uneven lambda_1 solves, batched)", value=per_hour,
+                          unit="instances/hour", n_gpus=1, steps=a.steps, warmup=a.warmup,
+                          higher_is_better=True, data="synthetic",
+                          config=dict(workload="batch: beta=1/m, m in {1,2,3,4} x N in {128,192,256,384}, k=16, "
+                                               "32N bits, moments -> LDL^T -> block -> lambda_1"),
+                          seconds_batched=times["batched"], seconds_sequential=times["sequential"],
+                          speedup=times["sequential"] / times["batched"])), flush=True)
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.profile_case:
+    if args.workload == "batch":
+        run_batch(args)
+    elif args.profile_case:
         profile_case(args)
     elif args.impl == "reference":
         run_reference(args)
