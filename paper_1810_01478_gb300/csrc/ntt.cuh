@@ -421,14 +421,20 @@ __device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, co
                                              uint32_t (&hi)[M]) {
   constexpr int n = 32 * M;
   const int lane = lane_id();
-  const int L = nc.L, st = ntt_stride(L);
+  constexpr int L = ntt_len(n), st = ntt_stride(L);
 #pragma unroll 1
   for (int q = 0; q < NTT_Q; ++q) {
     const uint32_t p = sel3(nc.p, q), pinv = sel3(nc.pinv, q);
     const uint4* a4 = reinterpret_cast<const uint4*>(fx + (size_t)q * L);
     const uint4* b4 = reinterpret_cast<const uint4*>(fy + (size_t)q * L);
     uint32_t* o = nb + q * st;
-    for (int k = lane; k < L / 4; k += 32) {
+    // a trip count known at compile time and the loop unrolled, so that all
+    // of a lane's loads of this prime are in flight together (one L2 round
+    // trip per prime instead of one per iteration)
+#pragma unroll
+    for (int it = 0; it < (L / 4 + 31) / 32; ++it) {
+      const int k = lane + 32 * it;
+      if ((L / 4) % 32 != 0 && k >= L / 4) break;
       const uint4 a = X_RO ? ld_stream(a4 + k) : a4[k], b = ld_stream(b4 + k);
       const int i = npad(4 * k);  // the four words share one padding block
       o[i] = mont_mul_lazy(a.x, b.x, p, pinv);
