@@ -311,20 +311,26 @@ __device__ __forceinline__ void warp_ntt_inv(uint32_t* buf, const NttConst& nc, 
 template <int M>
 __device__ __forceinline__ void warp_ntt_number(const uint32_t* __restrict__ mant, uint32_t* buf,
                                                 uint32_t* __restrict__ out, const NttConst& nc, bool scaled) {
-  constexpr int n = 32 * M;
+  constexpr int n = 32 * M, L = ntt_len(n);
   const int lane = lane_id();
+  // the mantissa once, coalesced, into registers (limb lane + 32 t)
+  uint32_t mv[M];
+#pragma unroll
+  for (int t = 0; t < M; ++t) mv[t] = mant[lane + 32 * t];
 #pragma unroll 1
   for (int q = 0; q < NTT_Q; ++q) {
     const uint32_t p = sel3(nc.p, q), rl = sel3(nc.rl, q), rls = sel3(nc.rls, q);
-    for (int k = lane; k < ntt_len(n); k += 32) {
-      uint32_t v = k < n ? mant[k] : 0u;
+#pragma unroll
+    for (int t = 0; t < L / 32; ++t) {
+      const int k = lane + 32 * t;
+      uint32_t v = t < M ? mv[t < M ? t : 0] : 0u;
       v = v >= 2 * p ? v - 2 * p : v;  // 2^32 < 4p: now in [0, 2p)
       buf[npad(ntt_pos<n>(k))] = v >= 2 * p ? v - 2 * p : v;
     }
     __syncwarp();
     warp_ntt_fwd<ntt_logk(n), ntt_rows(n)>(buf, nc, q);
-    uint32_t* o = out + (size_t)q * nc.L;
-    for (int k = lane; k < nc.L; k += 32) {
+    uint32_t* o = out + (size_t)q * L;
+    for (int k = lane; k < L; k += 32) {
       uint32_t v = buf[npad(k)];
       v = v >= p ? v - p : v;
       o[k] = scaled ? mul_shoup(v, rl, rls, p) : v;
