@@ -5,10 +5,11 @@ beyond the oracle's reach, so it is checked on samples the oracle can compute
 one by one: factor entries L[r][c] (and pivots) by Algorithm 1 on the index
 set {0..c} U {r} (oracle.ldlt.sample_entry, which reproduces the full
 factor's entry exactly), the first 40 rows of X (which depend only on the
-leading 40 x 40 block), lambda_1..3 against the oracle's N = 1024 run
+leading 40 x 40 block), lambda_1..3 against the oracle's N = 1024 runs
 (tests/golden/c5_1024_*.json, accurate far beyond 1e-40 at 4096 bits), and
-the gradient by precision doubling.  At 4096 bits the whole N = 1024 factor
-and X are compared bit for bit through their SHA-256 digests.
+the gradient by precision doubling.  At 4096 bits (schoolbook products) and
+8192 bits (NTT products) the whole N = 1024 factor and X are compared bit for
+bit through their SHA-256 digests.
 """
 import json
 import os
@@ -93,16 +94,19 @@ def test_bench_workload_sampled_parity():
         h.close()
 
 
-def test_full_factor_bit_exact_at_4096_bits():
+@pytest.mark.parametrize("bits", [4096, 8192])
+def test_full_factor_bit_exact(bits):
+    """The whole N = 1024 factor and X bit for bit: at 4096 bits with
+    schoolbook products, at 8192 bits with NTT products."""
     import paper_1810_01478_gb300 as hk
     from tests.digest import factor_digest, x_digest
-    gd = golden("c5_1024_4096")
+    gd = golden("c5_1024_%d" % bits)
     hk.load()
-    h, lam, _ = run(hk, 4096)
+    h, lam, _ = run(hk, bits)
     try:
         assert factor_digest(h, hk, N) == gd["factor_sha256"]
         assert x_digest(h, hk, N, K) == gd["x_sha256"]
-        with mpm.workprec(8192):
+        with mpm.workprec(2 * bits):
             for j in range(3):
                 want = mpm.mpf(gd["lambdas"][j])
                 assert abs(value(lam[0][j], lam[1][j], lam[2][j]) - want) / want < TOL
