@@ -146,3 +146,28 @@ def test_config2_and_4_against_golden():
                 assert abs(got_g - want) / abs(want) < LAMBDA_TOL, key
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("bits", [1024, 8192])
+@pytest.mark.parametrize("N,k,n_eig", [(1, 1, 1), (2, 1, 1), (2, 2, 2), (5, 1, 1), (3, 3, 3)])
+def test_degenerate_sizes_vs_oracle(N, k, n_eig, bits):
+    """Smallest cases: N = 1 (no trailing update), k = 1 (the (k-1) block is
+    empty: no truncation estimate), k = N (the whole inverse); at a
+    schoolbook width and at an NTT width."""
+    import math
+    import paper_1810_01478_gb300 as hk
+    ref = PL.run(Fraction(1, 2), N, k, bits // 32, n_eig=n_eig)
+    h, lam, _ = run_path(hk, (1, 2), N, k, bits, n_eig=n_eig)
+    try:
+        s, e, m, f64, terr = lam
+        with mpm.workprec(ref["prec"]):
+            for j in range(n_eig):
+                got = gpu_mpf(s[j], e[j], m[j])
+                assert abs(got - ref["lambdas"][j]) / ref["lambdas"][j] < LAMBDA_TOL, j
+                want_t = ref["trunc_errors"][j]
+                if want_t is None:
+                    assert math.isnan(terr[j])
+                else:
+                    assert abs(terr[j] - float(want_t)) <= 1e-6 * abs(float(want_t))
+    finally:
+        h.close()
