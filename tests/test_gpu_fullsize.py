@@ -112,3 +112,27 @@ def test_full_factor_bit_exact(bits):
                 assert abs(value(lam[0][j], lam[1][j], lam[2][j]) - want) / want < TOL
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("n_", [512, 768])
+def test_sweep_sizes(n_):
+    """The paper-scale sweep sizes N = 512, 768 (k = 32): the whole factor and
+    X bit for bit at 4096 bits, and lambda_1..3 at 24576 bits against the
+    oracle's 4096-bit values (accurate far beyond 1e-40 at these N)."""
+    import paper_1810_01478_gb300 as hk
+    from tests.digest import factor_digest, x_digest
+    gd = golden("c5_%d_4096" % n_)
+    hk.load()
+    for bits in (4096, 24576):
+        with hk.Hankel(0) as h:
+            h.moments(1, 2, n_, bits)
+            h.ldlt()
+            h.inv_block(K)
+            s, e, m, _, _ = h.lambda1(3)
+            if bits == 4096:
+                assert factor_digest(h, hk, n_) == gd["factor_sha256"]
+                assert x_digest(h, hk, n_, K) == gd["x_sha256"]
+            with mpm.workprec(2 * bits):
+                for j in range(3):
+                    want = mpm.mpf(gd["lambdas"][j])
+                    assert abs(value(s[j], e[j], m[j]) - want) / want < TOL, (n_, bits, j)
