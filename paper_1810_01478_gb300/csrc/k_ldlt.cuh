@@ -131,9 +131,56 @@ __global__ void k_assemble(MPVec mu, MPVec A, int N) {
 // ---------------------------------------------------------------------------
 // pivot reciprocal (one warp): R_i for d_i = A[i][i]
 // ---------------------------------------------------------------------------
-// rec: n limbs of R, then (sh) in rec_meta[0].
+// Products of the reciprocal's full-width steps through transforms held in
+// shared memory: fd = F(D') (formed once), fr = F(R) (scaled), fx = F(x).
 template <int M>
-__global__ void k_recip_pivot(MPVec A, int N, int i, uint32_t* rec, int* rec_meta, int* err) {
+struct RecipNtt {
+  NttConst nc;
+  uint32_t *fd, *fr, *fx, *nb, *stage;
+  bool have_d;
+  __device__ bool wide(int w) const { return w == 32 * M; }
+  template <int MM>
+  __device__ void set_r(const uint32_t* ys) {
+    warp_ntt_number<M>(ys, nb, fr, nc, true);
+    __syncwarp();
+  }
+  __device__ void transform(const uint32_t (&x)[M], uint32_t* out) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) stage[lane_id() * M + k] = x[k];
+    __syncwarp();
+    warp_ntt_number<M>(stage, nb, out, nc, false);
+    __syncwarp();
+  }
+  template <int MM>
+  __device__ void mul_d(const uint32_t (&dp)[M], uint32_t (&lo)[M], uint32_t (&hi)[M]) {
+    if (!have_d) {
+      transform(dp, fd);
+      have_d = true;
+    }
+    warp_mul_ntt<M, false, false>(fd, fr, nb, nc, lo, hi);
+    __syncwarp();
+  }
+  template <int MM>
+  __device__ void mul_r(const uint32_t (&x)[M], uint32_t (&lo)[M], uint32_t (&hi)[M]) {
+    transform(x, fx);
+    warp_mul_ntt<M, false, false>(fx, fr, nb, nc, lo, hi);
+    __syncwarp();
+  }
+};
+
+// shared-memory words of k_recip_pivot: ys, sp (schoolbook), and with NTT
+// products a staging area, three transforms and the product's work area
+template <int M>
+__host__ __device__ constexpr size_t recip_pivot_words(bool ntt) {
+  return ntt ? (size_t)4 * (32 * M) + 4 + 3 * (size_t)NTT_Q * ntt_len(32 * M) + (size_t)NTT_Q * ntt_stride(ntt_len(32 * M))
+             : (size_t)3 * (32 * M) + 4;
+}
+
+// rec: n limbs of R, then (sh) in rec_meta[0].  use_ntt: the full-width
+// steps take NTT products (shared memory of recip_pivot_words(true)).
+template <int M>
+__global__ void k_recip_pivot(MPVec A, int N, int i, uint32_t* rec, int* rec_meta, int* err, NttConst nc,
+                              int use_ntt) {
   constexpr int n = 32 * M;
   extern __shared__ uint32_t smem[];
   uint32_t* ys = smem;
@@ -147,7 +194,15 @@ __global__ void k_recip_pivot(MPVec A, int N, int i, uint32_t* rec, int* rec_met
     return;
   }
   int sh;
-  warp_recip<M>(dc, ys, sp, R, sh, err);
+  if (use_ntt) {
+    constexpr int L = ntt_len(n);
+    uint32_t* stage = smem + 3 * n + 4;
+    uint32_t* fd = stage + n;
+    RecipNtt<M> pol{nc, fd, fd + NTT_Q * L, fd + 2 * NTT_Q * L, fd + 3 * NTT_Q * L, stage, false};
+    warp_recip_p<M>(dc, ys, sp, R, sh, err, pol);
+  } else {
+    warp_recip<M>(dc, ys, sp, R, sh, err);
+  }
   store_chunk<M>(rec, R);
   if (lane_id() == 0) rec_meta[0] = sh;
 }

@@ -100,9 +100,33 @@ __device__ __forceinline__ void read_shifted(const uint32_t* sp, int w, int b, u
 // sh = leading zero bits of D's top limb and R = min(floor(2^(64n-1)/D'),
 // 2^(32n)-1), D' = D << sh.  ys: n words of this warp's smem (R lives there
 // between products); sp: 2n+1 words of scratch.  Sets *err on a bound overrun.
+// Products of the full-width steps: `wide(w)` says whether steps at width w
+// take them from the policy (set_r: R is in ys; mul_d: D' R; mul_r: x R);
+// the default forms every product with warp_mul.
+struct RecipSchoolbook {
+  __device__ bool wide(int) const { return false; }
+  template <int M>
+  __device__ void set_r(const uint32_t*) {}
+  template <int M>
+  __device__ void mul_d(const uint32_t (&)[M], uint32_t (&)[M], uint32_t (&)[M]) {}
+  template <int M>
+  __device__ void mul_r(const uint32_t (&)[M], uint32_t (&)[M], uint32_t (&)[M]) {}
+};
+
+template <int M, class P>
+__device__ void warp_recip_p(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, uint32_t (&R)[M], int& sh,
+                             int* err, P& prod);
+
 template <int M>
 __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, uint32_t (&R)[M], int& sh,
                            int* err) {
+  RecipSchoolbook pol;
+  warp_recip_p<M>(d, ys, sp, R, sh, err, pol);
+}
+
+template <int M, class P>
+__device__ void warp_recip_p(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, uint32_t (&R)[M], int& sh,
+                             int* err, P& prod) {
   constexpr int n = 32 * M;
   const int lane = lane_id();
   // D' = D << sh
@@ -161,10 +185,17 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
     for (int k = 0; k < M; ++k) ys[lane * M + k] = R[k];
     __syncwarp();
     uint32_t plo[M], phi[M], elo[M], ehi[M];
-    warp_mul<M>(dp, ys, sp, plo, phi);
+    const bool wide = prod.wide(w);
+    if (wide) {
+      prod.template set_r<M>(ys);
+      prod.template mul_d<M>(dp, plo, phi);
+    } else {
+      warp_mul<M>(dp, ys, sp, plo, phi);
+    }
     dsub<M>(clo, chi, plo, phi, elo, ehi);  // E >= 0 while R <= floor(C/D')
     uint32_t qlo[M], qhi[M];
-    warp_mul<M>(ehi, ys, sp, qlo, qhi);          // (E >> 32n) * R
+    if (wide) prod.template mul_r<M>(ehi, qlo, qhi);
+    else warp_mul<M>(ehi, ys, sp, qlo, qhi);  // (E >> 32n) * R
     // corr = floor(Q / 2^(32n-1)) = (Q >> (32n)) * 2 + top bit of Q's limb n-1
     uint32_t corr[M];
     {
@@ -201,7 +232,12 @@ __device__ void warp_recip(const uint32_t (&d)[M], uint32_t* ys, uint32_t* sp, u
     for (int k = 0; k < M; ++k) ys[lane * M + k] = R[k];
     __syncwarp();
     uint32_t plo[M], phi[M], elo[M], ehi[M];
-    warp_mul<M>(dp, ys, sp, plo, phi);
+    if (prod.wide(n)) {
+      prod.template set_r<M>(ys);
+      prod.template mul_d<M>(dp, plo, phi);
+    } else {
+      warp_mul<M>(dp, ys, sp, plo, phi);
+    }
     const bool negative = dsub<M>(clo, chi, plo, phi, elo, ehi);
     __syncwarp();
     if (negative) {  // cannot happen when R stays below the true value

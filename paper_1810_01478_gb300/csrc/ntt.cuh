@@ -419,9 +419,10 @@ __device__ __forceinline__ uint32_t crt_chunk(const uint32_t* W, int k0, uint32_
 // Exact product P = X * Y from their stored transforms (fx: unscaled, fy:
 // scaled by 2^32/L), in the lo/hi chunk layout of warp_mul.  nb:
 // 3 ntt_stride(L) words of this warp's shared memory.
-// X_RO: fx is read-only for the whole kernel (else it was written by this
-// warp earlier in the kernel and is read through the coherent path).
-template <int M, bool X_RO = true>
+// X_RO / Y_RO: fx / fy is global memory that is read-only for the whole
+// kernel; otherwise (written by this warp earlier, or shared memory) it is
+// read through the generic path.
+template <int M, bool X_RO = true, bool Y_RO = true>
 __device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, const uint32_t* __restrict__ fy,
                                              uint32_t* nb, const NttConst& nc, uint32_t (&lo)[M],
                                              uint32_t (&hi)[M]) {
@@ -441,7 +442,7 @@ __device__ __forceinline__ void warp_mul_ntt(const uint32_t* __restrict__ fx, co
     for (int it = 0; it < (L / 4 + 31) / 32; ++it) {
       const int k = lane + 32 * it;
       if ((L / 4) % 32 != 0 && k >= L / 4) break;
-      const uint4 a = X_RO ? ld_stream(a4 + k) : a4[k], b = ld_stream(b4 + k);
+      const uint4 a = X_RO ? ld_stream(a4 + k) : a4[k], b = Y_RO ? ld_stream(b4 + k) : b4[k];
       const int i = npad(4 * k);  // the four words share one padding block
       o[i] = mont_mul_lazy(a.x, b.x, p, pinv);
       o[i + 1] = mont_mul_lazy(a.y, b.y, p, pinv);

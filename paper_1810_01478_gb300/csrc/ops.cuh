@@ -200,8 +200,10 @@ struct Ops {
     uint32_t* FB = c.ntt_buf ? c.ntt_buf + per * (size_t)N : nullptr;
     uint32_t* FRD = c.ntt_buf ? c.ntt_buf + 2 * per * (size_t)N : nullptr;
     // the reciprocal of pivot i and, for NTT quotients, the transforms of R and d_i
+    const size_t rp_smem = recip_pivot_words<M>(ntt) * 4;
+    if ((st = check_cuda(c, allow_smem(k_recip_pivot<M>, rp_smem), "smem attribute")) != HK_OK) return st;
     auto pivot = [&](int i) {
-      k_recip_pivot<M><<<1, 32, recip_smem, c.aux>>>(c.A.view(), N, i, c.rec, c.rec_meta, c.d_err);
+      k_recip_pivot<M><<<1, 32, rp_smem, c.aux>>>(c.A.view(), N, i, c.rec, c.rec_meta, c.d_err, nc, ntt ? 1 : 0);
       if (ntt) {
         k_ntt_pivot<M><<<1, 64, 2 * ntt_stride(nc.L) * 4, c.aux>>>(c.rec, c.A.view(), tri_pos(N, i, i), FRD, nc);
         count_launch(c);
@@ -309,7 +311,7 @@ struct Ops {
       k_assemble<M><<<grid, 256, 0, s>>>(mu, A, N);
     }
     for (int i = 0; i < N; ++i) {
-      k_recip_pivot<M><<<1, 32, recip_smem, s>>>(A, N, i, rec, rec_meta, err);
+      k_recip_pivot<M><<<1, 32, recip_smem, s>>>(A, N, i, rec, rec_meta, err, NttConst{}, 0);
       if (i == N - 1) break;
       const int64_t rows = N - 1 - i;
       const int gs = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, scale_res);
