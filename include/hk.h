@@ -23,7 +23,12 @@
  *
  * Streams.  Every call is ordered on the cudaStream_t given to hk_create
  * (borrowed, never destroyed).  hk_lambda1, hk_lambda1_grad and hk_export
- * synchronise that stream; the other calls only enqueue work.
+ * synchronise that stream; the other calls only enqueue work.  Internally the
+ * LDL^T at NTT widths runs on high-priority streams of the context, forked
+ * from and joined back to that stream, and hk_inv_block runs Algorithm 4 on a
+ * low-priority stream beside the still-running factorisation (each step
+ * after its column of L is final) before joining back: results are as if
+ * everything ran on the caller's stream.
  *
  * Errors.  Calls return hk_status; nothing aborts, traps or throws.  The
  * context keeps the first error (sticky) and hk_last_error describes it.
@@ -169,9 +174,10 @@ HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 
 /* Exact limb products of the factorisation and of hk_fused_batch, chosen
  * process-wide: HK_PRODUCT_SCHOOLBOOK (n^2 32x32-bit limb products, warp
- * operand scanning), HK_PRODUCT_NTT (number-theoretic transform modulo three
- * 31-bit primes and Chinese remaindering; the transforms of a step's pivot
- * column are computed once and reused by every update, n <= 1024 limbs), or
+ * operand scanning), HK_PRODUCT_NTT (number-theoretic transforms of length
+ * 2^a or 3 2^a modulo three primes k 3 2^11 + 1 below 2^30 and Chinese
+ * remaindering; the transforms of a step's pivot column are computed once and
+ * reused by every update, n <= 1024 limbs), or
  * HK_PRODUCT_AUTO (the NTT from HK_NTT_AUTO_MIN_M * 1024 bits up).  Both give
  * the same exact product, so results are identical bit for bit; this only
  * changes speed.  The paper's GMP multiplies likewise switch algorithm by size. */
