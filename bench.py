@@ -273,15 +273,16 @@ def run_ours(a):
     updates_per_launch = macs_per_launch / (n * n)
     achieved_sb = macs_per_launch / (avg_launch_ms / 1e3) / 1e12
     ntt = (a.bits // 1024) >= hk.HK_NTT_AUTO_MIN_M
-    traffic = None
+    traffic = issue = None
     tp = os.path.join(ROOT, "profiles", "trailing_traffic.json")
     if os.path.exists(tp):
         try:
             t = json.load(open(tp))
             if t.get("bits") == a.bits and t.get("kernel_source_sha") == kernel_sha():
                 traffic = t["bytes_per_update"] * updates_per_launch
+                issue = t.get("issue_active_frac")
         except (ValueError, KeyError):
-            traffic = None
+            traffic = issue = None
     schoolbook = dict(achieved=achieved_sb, peak=peak_sb, unit="Tlimb-MAC/s", frac=achieved_sb / peak_sb,
                       note=f"n^2 = {n * n} limb products per update (the schoolbook-equivalent convention); "
                            f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_LIMB_MAC} IMAD per limb "
@@ -296,6 +297,9 @@ def run_ours(a):
                                         f"{ntt_shape(n)[1]})",
                         peak_note=f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_MODMUL} IMAD per "
                                   f"modular multiplication x {sm_max:.0f} MHz (derived, not measured)",
+                        issue_active_frac=issue,
+                        issue_note="fraction of cycles the kernel issues an instruction (ncu capture of the same "
+                                   "kernel source, profiles/trailing_traffic.json): the bound it actually meets",
                         schoolbook_equiv=schoolbook)
     else:
         roofline = dict(bound="alu", achieved=achieved_sb, peak=peak_sb, unit="Tlimb-MAC/s",
