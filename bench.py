@@ -75,7 +75,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-case", action="store_true",
                     help="only run moments + LDL^T once at --N/--bits (a small case for ncu captures)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+    ap.add_argument("--rows", default="",
+                    help="table2: comma-separated N values of Table 2 to run (default: all nine)")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "table2"],
                     help="batch: 16 uneven instances (beta = 1/m, m in 1..4, N in {128..384}, k = 16, "
                          "32 N bits) through hk_batch_run, beside the same instances one by one")
     return ap.parse_args()
@@ -400,9 +402,60 @@ def run_batch(a):
                           speedup=times["sequential"] / times["batched"])), flush=True)
 
 
+def run_table2(a):
+    """The paper's Table 2 (Sec. 5.1) on one GPU: beta = 1/2, N = 500 ... 4500,
+    k = 8, at twice the table's fixed-point bits K (the paper's fixed point
+    keeps 2K bits during the LDL^T, Sec. 4.1), rounded up to a compiled width.
+    Prints one JSON line per row (the three eigenvalues and truncation
+    estimates against the printed ones, and the wall time of the solve) and
+    then the Sec. 6.1 fit y = a + b x, x = log(4 pi N e),
+    y = log(8 pi sqrt(log N) / lambda_1), N^2-weighted, on these lambda_1."""
+    import math
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1810_01478_gb300 as hk
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_beta_half.json")))
+    widths = sorted(hk.hk_supported_bits())
+    want = [int(x) for x in a.rows.split(",") if x] if a.rows else None
+    pts = []
+    for row in table["rows"]:
+        N = row["N"]
+        if want and N not in want:
+            continue
+        bits = next(w for w in widths if w >= 2 * row["bits"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with hk.Hankel(0) as h:
+            h.moments(1, 2, N, bits)
+            h.ldlt()
+            h.inv_block(8)
+            _, _, _, lam, terr = h.lambda1(3)
+        dt = time.perf_counter() - t0
+        printed = [float(v) for v in row["lambda"]]
+        pts.append((N, float(lam[0])))
+        print(json.dumps(dict(workload="table2", N=N, bits=bits, k=8, seconds=dt,
+                              lambda_f64=[float(v) for v in lam], lambda_printed=row["lambda"],
+                              rel_diff=[abs(float(lam[j]) - printed[j]) / printed[j] for j in range(3)],
+                              trunc_err_f64=[float(v) for v in terr], trunc_err_printed=row["trunc_err"])),
+              flush=True)
+    if len(pts) >= 2:
+        xs = [math.log(4 * math.pi * N * math.e) for N, _ in pts]
+        ys = [math.log(8 * math.pi * math.sqrt(math.log(N)) / l1) for N, l1 in pts]
+        ws = [N * N for N, _ in pts]
+        sw = sum(ws)
+        mx = sum(w * x for w, x in zip(ws, xs)) / sw
+        my = sum(w * y for w, y in zip(ws, ys)) / sw
+        b = sum(w * (x - mx) * (y - my) for w, x, y in zip(ws, xs, ys)) / sum(w * (x - mx) ** 2 for w, x in zip(ws, xs))
+        print(json.dumps(dict(workload="table2_fit", rows=[N for N, _ in pts], intercept=my - b * mx, slope=b,
+                              paper=table["fit"])), flush=True)
+
+
 if __name__ == "__main__":
     args = parse()
-    if args.workload == "batch":
+    if args.workload == "table2":
+        run_table2(args)
+    elif args.workload == "batch":
         run_batch(args)
     elif args.profile_case:
         profile_case(args)
