@@ -148,9 +148,19 @@ HK_API hk_status hk_lambda1(hk_ctx* ctx, int n_eig, int32_t* sign, int32_t* exp,
 /* a8. d lambda_1 / d beta of the block estimate lambda_1 = 1/nu_1:
  * (w^T Hdot w)/nu_1^2 with w = L^{-T} D^{-1} X u (u the unit eigenvector) and
  * Hdot_ij = d mu_{i+j}/d beta = -(mu/beta)(1 + x psi(x)), x = (i+j+1)/beta.
- * Needs beta = 1/m.  Outputs (host, may be NULL): one number, and its double.
- * Synchronises. */
+ * For beta = 1/m, psi(x) = H_{x-1} - gamma (x an integer); for beta = a/b
+ * (a > 1) psi(x) follows from psi(x + 1) = psi(x) + 1/x and the constants
+ * psi(r/a), r = 1..a-1, given beforehand with hk_set_psi_constants (else
+ * HK_ERR_UNSUPPORTED).  Outputs (host, may be NULL): one number, and its
+ * double.  Synchronises. */
 HK_API hk_status hk_lambda1_grad(hk_ctx* ctx, int32_t* sign, int32_t* exp, uint32_t* limbs, double* f64);
+
+/* The constants psi(r/a) (digamma), r = 1..a-1, for hk_lambda1_grad at
+ * beta = a/b: `count` numbers of nc limbs each (host, number layout above,
+ * copied before the call returns), truncated or zero-extended to the working
+ * width.  After the moments; count = a - 1. */
+HK_API hk_status hk_set_psi_constants(hk_ctx* ctx, int count, int nc, const int32_t* sign, const int32_t* exp,
+                                      const uint32_t* limbs);
 
 /* Copy count numbers starting at index first of `what` to host arrays.
  * Synchronises. */

@@ -26,16 +26,37 @@ from . import invblock as IB
 from . import eigen as EG
 
 
+def psi_gauss(r, m, mpm):
+    """psi(r/m) for 0 < r < m by Gauss's digamma theorem:
+    -gamma - ln(2m) - (pi/2) cot(pi r/m)
+           + 2 sum_{j=1}^{floor((m-1)/2)} cos(2 pi j r/m) ln sin(pi j/m)
+    (elementary functions only, so cheap at thousands of bits)."""
+    v = -mpm.euler - mpm.log(2 * m) - mpm.pi / 2 * mpm.cot(mpm.pi * r / m)
+    for j in range(1, (m - 1) // 2 + 1):
+        v += 2 * mpm.cos(2 * mpm.pi * j * r / m) * mpm.log(mpm.sin(mpm.pi * j / m))
+    return v
+
+
 def psi(x, mpm):
-    """Digamma at x: for a positive integer x the exact identity
+    """Digamma at x > 0.  A positive integer x: the exact identity
     psi(x) = H_{x-1} - gamma (harmonic number as an exact Fraction, Euler's
-    gamma from mpmath); otherwise mpmath.digamma."""
+    gamma from mpmath).  A non-integer Fraction x = q + r/m: the recurrence
+    psi(y + 1) = psi(y) + 1/y (from Gamma(y + 1) = y Gamma(y)) down to r/m,
+    the q reciprocals summed exactly, plus Gauss's theorem at r/m.
+    Anything else: mpmath.digamma."""
     if isinstance(x, int) or (isinstance(x, Fraction) and x.denominator == 1):
         x = int(x)
         h = Fraction(0)
         for j in range(1, x):
             h += Fraction(1, j)
         return mpm.mpf(h.numerator) / h.denominator - mpm.euler
+    if isinstance(x, Fraction) and x > 0:
+        m = x.denominator
+        q, r = divmod(x.numerator, m)
+        h = Fraction(0)
+        for i in range(q):
+            h += Fraction(m, r + i * m)
+        return psi_gauss(r, m, mpm) + mpm.mpf(h.numerator) / h.denominator
     return mpm.digamma(x)
 
 

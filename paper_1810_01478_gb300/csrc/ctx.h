@@ -38,6 +38,8 @@ struct Ctx {
   int64_t beta_num = 0, beta_den = 0;
   int* d_err = nullptr;       // device error flags (ErrBits)
   DevVec mu, A, U, X, S, evec, scratch;
+  DevVec psi;                 // psi(r/a), r = 1..a-1, for the gradient at beta = a/b (hk_set_psi_constants)
+  int psi_count = -1;
   uint32_t* rec = nullptr;    // pivot reciprocal scratch (n limbs)
   int* rec_meta = nullptr;
   // look-ahead: the next pivot's reciprocal runs on `aux` while the main

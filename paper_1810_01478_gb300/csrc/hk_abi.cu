@@ -270,6 +270,7 @@ void hk_destroy(hk_ctx* h) {
   dev_free(c.X);
   dev_free(c.S);
   dev_free(c.evec);
+  dev_free(c.psi);
   dev_free(c.scratch);
   for (auto& kv : c.pool) dev_free(kv.second);
   if (c.d_tasks) cudaFree(c.d_tasks);
@@ -340,6 +341,7 @@ hk_status hk_moments(hk_ctx* h, int64_t beta_num, int64_t beta_den, int N, int b
   c.beta_num = beta_num;
   c.beta_den = beta_den;
   c.stage = ST_MOMENTS;
+  c.psi_count = -1;
   return HK_OK;
 }
 
@@ -396,6 +398,48 @@ hk_status hk_moments_gamma(hk_ctx* h, int64_t beta_num, int64_t beta_den, int N,
   c.beta_num = beta_num;
   c.beta_den = beta_den;
   c.stage = ST_MOMENTS;
+  c.psi_count = -1;
+  return HK_OK;
+}
+
+hk_status hk_set_psi_constants(hk_ctx* h, int count, int nc, const int32_t* sign, const int32_t* exp,
+                               const uint32_t* limbs) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_set_psi_constants before the moments");
+  if (count < 0 || count > 63 || nc < 1 || nc > 4096 || (count && (!sign || !exp || !limbs)))
+    return set_error(c, HK_ERR_ARG, "psi constants: count in 0..63, nc >= 1, host arrays");
+  const int n = c.n;
+  // each constant truncated (or zero-extended) to the working width
+  std::vector<int32_t> s(count), e(count);
+  std::vector<uint32_t> m((size_t)count * n, 0u);
+  for (int r = 0; r < count; ++r) {
+    const uint32_t* src = limbs + (size_t)r * nc;
+    if (src[nc - 1] == 0u) {
+      for (int i = 0; i < nc; ++i)
+        if (src[i]) return set_error(c, HK_ERR_ARG, "psi constants must be normalised");
+      s[r] = 0;
+      e[r] = 0;
+      continue;
+    }
+    s[r] = sign[r] ? 1 : 0;
+    e[r] = exp[r] + (nc - n);
+    for (int i = 0; i < n; ++i) {
+      const int j = nc - n + i;
+      m[(size_t)r * n + i] = j >= 0 ? src[j] : 0u;
+    }
+  }
+  if (c.psi.count != count || c.psi.n != n) {
+    dev_free(c.psi);
+    if (count && (st = check_cuda(c, dev_alloc(c.psi, count, n), "allocating psi")) != HK_OK) return st;
+  }
+  if (count &&
+      ((st = check_cuda(c, cudaMemcpy(c.psi.sgn, s.data(), (size_t)count * 4, cudaMemcpyHostToDevice), "H2D")) ||
+       (st = check_cuda(c, cudaMemcpy(c.psi.exp, e.data(), (size_t)count * 4, cudaMemcpyHostToDevice), "H2D")) ||
+       (st = check_cuda(c, cudaMemcpy(c.psi.mant, m.data(), m.size() * 4, cudaMemcpyHostToDevice), "H2D"))))
+    return st;
+  c.psi_count = count;
   return HK_OK;
 }
 
@@ -417,6 +461,7 @@ hk_status hk_set_moments(hk_ctx* h, int N, int bits, const int32_t* sign, const 
   c.beta_num = beta_num;
   c.beta_den = beta_den;
   c.stage = ST_MOMENTS;
+  c.psi_count = -1;
   return HK_OK;
 }
 
@@ -473,8 +518,18 @@ hk_status hk_lambda1_grad(hk_ctx* h, int32_t* sign, int32_t* exp, uint32_t* limb
   if (st != HK_OK) return st;
   Ctx& c = h->c;
   if (c.stage < ST_LAMBDA) return set_error(c, HK_ERR_ORDER, "hk_lambda1_grad before hk_lambda1");
-  if (c.beta_den <= 0 || c.beta_num <= 0 || c.beta_den % c.beta_num != 0)
-    return set_error(c, HK_ERR_UNSUPPORTED, "the gradient needs beta = 1/m");
+  if (c.beta_den <= 0 || c.beta_num <= 0) return set_error(c, HK_ERR_UNSUPPORTED, "the gradient needs beta");
+  {
+    int64_t x = c.beta_num, y = c.beta_den;
+    while (y) {
+      const int64_t t = x % y;
+      x = y;
+      y = t;
+    }
+    const int64_t a = c.beta_num / x;
+    if (a > 1 && c.psi_count != a - 1)
+      return set_error(c, HK_ERR_UNSUPPORTED, "beta = a/b needs psi(r/a), r = 1..a-1 (hk_set_psi_constants)");
+  }
   const size_t pe0 = c.prof ? prof_mark(c) : 0;
   if ((st = ops_for(c.M)->grad(c, sign, exp, limbs, f64)) != HK_OK) return st;
   if (c.prof) c.stage_ev.push_back({4, {pe0, prof_mark(c)}});

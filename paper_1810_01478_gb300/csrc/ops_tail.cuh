@@ -486,16 +486,91 @@ struct Tail {
   //     w = L^{-T} D^{-1} X v,  Hdot_ij = mudot_{i+j},
   //     mudot_s = -m mu_s (1 + m(s+1) (H_{m(s+1)-1} - gamma))   for beta = 1/m
   // ------------------------------------------------------------------------
+  // mudot_s = d mu_s / d beta = -(b/a) mu_s (1 + x psi(x)), x = b(s+1)/a, for beta = a/b
+  // (a > 1) into Z[s].  psi(v/a) for v = 1..b(2N-1) is a prefix sum within each
+  // residue class mod a: the seeds psi(r/a) (r < a, c.psi) and psi(1) = -gamma
+  // at v = a, then psi(v/a) = psi((v-a)/a) + a/(v-a) (psi(x+1) = psi(x) + 1/x),
+  // summed by a Hillis-Steele scan with strides a, 2a, 4a, ...
+  static hk_status mudot_rational(Ctx& c, int64_t a, int64_t b, DevVec* H0, DevVec* H1, DevVec* hq, DevVec* kint,
+                                  DevVec* cst, DevVec* Z, DevVec* ONE) {
+    const int N = c.N;
+    const int64_t V = b * (2 * N - 1);
+    hk_status st;
+    // constants b/a and gamma
+    if ((st = small(c, {b}, {a}, cst->view())) != HK_OK) return st;
+    {
+      std::vector<uint32_t> g(n);
+      for (int i = 0; i < n; ++i) g[i] = hk_euler_gamma[HK_GAMMA_LIMBS - n + i];
+      const int32_t gs = 0, ge = -n;
+      if ((st = check_cuda(c, cudaMemcpyAsync(cst->sgn + 1, &gs, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+          (st = check_cuda(c, cudaMemcpyAsync(cst->exp + 1, &ge, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+          (st = check_cuda(c, cudaMemcpyAsync(cst->mant + n, g.data(), (size_t)n * 4, cudaMemcpyHostToDevice,
+                                              c.stream), "H2D")) ||
+          (st = check_cuda(c, cudaStreamSynchronize(c.stream), "H2D sync")))
+        return st;
+    }
+    // terms: a/(v-a) for v > a, 0 elsewhere; then the seeds at v = 1..a
+    {
+      std::vector<int64_t> num(V + 1), den(V + 1);
+      for (int64_t v = 0; v <= V; ++v) {
+        num[v] = v > a ? a : 0;
+        den[v] = v > a ? v - a : 1;
+      }
+      if ((st = small(c, num, den, H0->view())) != HK_OK) return st;
+      std::vector<ChainTask> seeds;
+      for (int64_t r = 1; r < a; ++r) seeds.push_back(ChainTask{r, r - 1, 0, 0, 0, 0, 0, 0});
+      if ((st = chains(c, seeds, ONE->view(), ONE->view(), c.psi.view(), H0->view())) != HK_OK) return st;
+      if ((st = chains(c, {ChainTask{a, 1, 0, 0, 0, 0, 0, CH_NEG_INIT}}, ONE->view(), ONE->view(), cst->view(),
+                       H0->view())) != HK_OK)
+        return st;
+    }
+    for (int64_t d = a; d <= V; d <<= 1) {
+      std::vector<ChainTask> t;
+      t.reserve(V + 1);
+      for (int64_t i = 0; i <= V; ++i)
+        t.push_back(i >= d ? ChainTask{i, i, i - d, 0, 0, 0, 1, CH_ADD} : ChainTask{i, i, 0, 0, 0, 0, 0, 0});
+      if ((st = chains(c, t, H0->view(), ONE->view(), H0->view(), H1->view())) != HK_OK) return st;
+      std::swap(*H0, *H1);
+    }
+    // h_s = psi(x_s); q_s = 1 + x_s h_s; p_s = mu_s q_s; mudot_s = -(b/a) p_s
+    std::vector<int64_t> kn, kd;
+    for (int s = 0; s <= 2 * N - 2; ++s) {
+      kn.push_back(b * (s + 1));
+      kd.push_back(a);
+    }
+    if ((st = small(c, kn, kd, kint->view())) != HK_OK) return st;
+    std::vector<ChainTask> t1, t2, t3, t4;
+    for (int s = 0; s <= 2 * N - 2; ++s) {
+      t1.push_back(ChainTask{s, b * (s + 1), 0, 0, 0, 0, 0, 0});          // psi(x_s)
+      t2.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ADD});                // 1 + x_s h_s
+      t3.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ZERO_INIT | CH_ADD}); // mu_s q_s
+      t4.push_back(ChainTask{s, 0, 0, s, 0, 0, 1, CH_ZERO_INIT});          // -(b/a) p_s
+    }
+    if ((st = chains(c, t1, ONE->view(), ONE->view(), H0->view(), hq->view())) != HK_OK) return st;
+    if ((st = chains(c, t2, kint->view(), hq->view(), ONE->view(), Z->view())) != HK_OK) return st;
+    if ((st = chains(c, t3, c.mu.view(), Z->view(), Z->view(), hq->view())) != HK_OK) return st;
+    return chains(c, t4, cst->view(), hq->view(), hq->view(), Z->view());
+  }
+
   static hk_status grad(Ctx& c, int32_t* osgn, int32_t* oexp, uint32_t* omant, double* of64) {
     const int N = c.N, k = c.k;
-    const int64_t m = c.beta_den / c.beta_num;
+    // beta = a/b in lowest terms; a = 1 is beta = 1/m (m = b)
+    int64_t ga = c.beta_num, gb = c.beta_den;
+    while (gb) {
+      const int64_t t = ga % gb;
+      ga = gb;
+      gb = t;
+    }
+    const int64_t a = c.beta_num / ga, b = c.beta_den / ga;
+    const int64_t m = b;
     hk_status st;
     DevVec* Rd = pool_get(c, "recip_d", N);
     DevVec* E1 = pool_get(c, "eig1", 2);
     DevVec* z = pool_get(c, "gz", 2 * N - 1);  // z = X v (N), later q_s and mudot_s (2N-1)
     DevVec* y = pool_get(c, "gy", N);
     DevVec* cs = pool_get(c, "gc", 2 * N - 1);
-    const int64_t tmax = m * (2 * N - 1) - 1;
+    // scan length: H_t for t <= m(2N-1) - 1 (a = 1), or psi(v/a) for v <= b(2N-1)
+    const int64_t tmax = (a == 1) ? m * (2 * N - 1) - 1 : b * (2 * N - 1);
     DevVec* H0 = pool_get(c, "gh0", tmax + 1);
     DevVec* H1 = pool_get(c, "gh1", tmax + 1);
     DevVec* hq = pool_get(c, "ghq", 2 * N - 1);
@@ -555,49 +630,53 @@ struct Tail {
       cd.push_back(Dot{s, lo, s - lo, 1, -1, hi - lo + 1, false});
     }
     if ((st = dots(c, cd, y->view(), y->view(), cs->view(), 0, N, N)) != HK_OK) return st;
-    // harmonic numbers H_t = sum_{j<=t} 1/j (Hillis-Steele scan of the reciprocals)
-    {
-      std::vector<int64_t> num(tmax + 1, 1), den(tmax + 1);
-      num[0] = 0;
-      for (int64_t j = 0; j <= tmax; ++j) den[j] = j ? j : 1;
-      if ((st = small(c, num, den, H0->view())) != HK_OK) return st;
-      for (int64_t d = 1; d <= tmax; d <<= 1) {
-        std::vector<ChainTask> t;
-        t.reserve(tmax + 1);
-        for (int64_t i = 0; i <= tmax; ++i)
-          t.push_back(i >= d ? ChainTask{i, i, i - d, 0, 0, 0, 1, CH_ADD} : ChainTask{i, i, 0, 0, 0, 0, 0, 0});
-        if ((st = chains(c, t, H0->view(), ONE->view(), H0->view(), H1->view())) != HK_OK) return st;
-        std::swap(*H0, *H1);
+    if (a == 1) {
+      // harmonic numbers H_t = sum_{j<=t} 1/j (Hillis-Steele scan of the reciprocals)
+      {
+        std::vector<int64_t> num(tmax + 1, 1), den(tmax + 1);
+        num[0] = 0;
+        for (int64_t j = 0; j <= tmax; ++j) den[j] = j ? j : 1;
+        if ((st = small(c, num, den, H0->view())) != HK_OK) return st;
+        for (int64_t d = 1; d <= tmax; d <<= 1) {
+          std::vector<ChainTask> t;
+          t.reserve(tmax + 1);
+          for (int64_t i = 0; i <= tmax; ++i)
+            t.push_back(i >= d ? ChainTask{i, i, i - d, 0, 0, 0, 1, CH_ADD} : ChainTask{i, i, 0, 0, 0, 0, 0, 0});
+          if ((st = chains(c, t, H0->view(), ONE->view(), H0->view(), H1->view())) != HK_OK) return st;
+          std::swap(*H0, *H1);
+        }
       }
+      // constants m and gamma
+      if ((st = small(c, {m}, {1}, cst->view())) != HK_OK) return st;
+      {
+        std::vector<uint32_t> g(n);
+        for (int i = 0; i < n; ++i) g[i] = hk_euler_gamma[HK_GAMMA_LIMBS - n + i];
+        const int32_t gs = 0, ge = -n;
+        if ((st = check_cuda(c, cudaMemcpyAsync(cst->sgn + 1, &gs, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+            (st = check_cuda(c, cudaMemcpyAsync(cst->exp + 1, &ge, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
+            (st = check_cuda(c, cudaMemcpyAsync(cst->mant + n, g.data(), (size_t)n * 4, cudaMemcpyHostToDevice,
+                                                c.stream), "H2D")) ||
+            (st = check_cuda(c, cudaStreamSynchronize(c.stream), "H2D sync")))
+          return st;
+      }
+      // h_s = H_{m(s+1)-1} - gamma ; q_s = 1 + m(s+1) h_s ; p_s = mu_s q_s ; mudot_s = -m p_s
+      std::vector<int64_t> kn, kd;
+      for (int s = 0; s <= 2 * N - 2; ++s) { kn.push_back(m * (s + 1)); kd.push_back(1); }
+      if ((st = small(c, kn, kd, kint->view())) != HK_OK) return st;
+      std::vector<ChainTask> t1, t2, t3, t4;
+      for (int s = 0; s <= 2 * N - 2; ++s) {
+        t1.push_back(ChainTask{s, m * (s + 1) - 1, 1, 0, 0, 0, 1, 0});             // H - gamma*1
+        t2.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ADD});                      // 1 + kint*h
+        t3.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ZERO_INIT | CH_ADD});       // mu*q
+        t4.push_back(ChainTask{s, 0, 0, s, 0, 0, 1, CH_ZERO_INIT});                // -m*p
+      }
+      if ((st = chains(c, t1, cst->view(), ONE->view(), H0->view(), hq->view())) != HK_OK) return st;
+      if ((st = chains(c, t2, kint->view(), hq->view(), ONE->view(), z->view())) != HK_OK) return st;
+      if ((st = chains(c, t3, c.mu.view(), z->view(), z->view(), hq->view())) != HK_OK) return st;
+      if ((st = chains(c, t4, cst->view(), hq->view(), hq->view(), z->view())) != HK_OK) return st;
+    } else if ((st = mudot_rational(c, a, b, H0, H1, hq, kint, cst, z, ONE)) != HK_OK) {
+      return st;
     }
-    // constants m and gamma
-    if ((st = small(c, {m}, {1}, cst->view())) != HK_OK) return st;
-    {
-      std::vector<uint32_t> g(n);
-      for (int i = 0; i < n; ++i) g[i] = hk_euler_gamma[HK_GAMMA_LIMBS - n + i];
-      const int32_t gs = 0, ge = -n;
-      if ((st = check_cuda(c, cudaMemcpyAsync(cst->sgn + 1, &gs, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
-          (st = check_cuda(c, cudaMemcpyAsync(cst->exp + 1, &ge, 4, cudaMemcpyHostToDevice, c.stream), "H2D")) ||
-          (st = check_cuda(c, cudaMemcpyAsync(cst->mant + n, g.data(), (size_t)n * 4, cudaMemcpyHostToDevice,
-                                              c.stream), "H2D")) ||
-          (st = check_cuda(c, cudaStreamSynchronize(c.stream), "H2D sync")))
-        return st;
-    }
-    // h_s = H_{m(s+1)-1} - gamma ; q_s = 1 + m(s+1) h_s ; p_s = mu_s q_s ; mudot_s = -m p_s
-    std::vector<int64_t> kn, kd;
-    for (int s = 0; s <= 2 * N - 2; ++s) { kn.push_back(m * (s + 1)); kd.push_back(1); }
-    if ((st = small(c, kn, kd, kint->view())) != HK_OK) return st;
-    std::vector<ChainTask> t1, t2, t3, t4;
-    for (int s = 0; s <= 2 * N - 2; ++s) {
-      t1.push_back(ChainTask{s, m * (s + 1) - 1, 1, 0, 0, 0, 1, 0});             // H - gamma*1
-      t2.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ADD});                      // 1 + kint*h
-      t3.push_back(ChainTask{s, 0, s, s, 0, 0, 1, CH_ZERO_INIT | CH_ADD});       // mu*q
-      t4.push_back(ChainTask{s, 0, 0, s, 0, 0, 1, CH_ZERO_INIT});                // -m*p
-    }
-    if ((st = chains(c, t1, cst->view(), ONE->view(), H0->view(), hq->view())) != HK_OK) return st;
-    if ((st = chains(c, t2, kint->view(), hq->view(), ONE->view(), z->view())) != HK_OK) return st;
-    if ((st = chains(c, t3, c.mu.view(), z->view(), z->view(), hq->view())) != HK_OK) return st;
-    if ((st = chains(c, t4, cst->view(), hq->view(), hq->view(), z->view())) != HK_OK) return st;
     // g = sum_s mudot_s c_s ; t = nu^2 (v^T v) ; result = g / t
     if ((st = dots(c, {Dot{0, 0, 0, 1, 1, 2 * N - 1, false}}, z->view(), cs->view(), res->view())) != HK_OK)
       return st;

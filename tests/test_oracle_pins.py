@@ -241,6 +241,13 @@ def test_psi_integer_identity_matches_digamma():
         for x in [1, 2, 3, 10, 41, 200]:
             assert abs(GR.psi(x, mpm) - mpm.digamma(x)) < mpm.mpf(2) ** -580
         assert abs(GR.psi(Fraction(9, 4), mpm) - mpm.digamma(mpm.mpf(9) / 4)) < mpm.mpf(2) ** -580
+        # rational x = q + r/m: the recurrence down to r/m and Gauss's theorem there
+        for m in (2, 3, 4, 9, 20):
+            for r in range(1, m):
+                for q in (0, 1, 7):
+                    x = Fraction(q * m + r, m)
+                    want = mpm.digamma(mpm.mpf(x.numerator) / x.denominator)
+                    assert abs(GR.psi(x, mpm) - want) < mpm.mpf(2) ** -580, (q, r, m)
 
 
 def test_gradient_closed_form_n2():
@@ -268,5 +275,21 @@ def test_gradient_analytic_vs_finite_difference():
     X = IB.partial_inverse(L, N, k, n)
     with mpm.workprec(1200):
         g, _, _ = GR.analytic_grad(beta, lambda s: 2 * mpm.factorial(2 * s + 1), L, D, X, k, n)
+        fd = GR.fd_grad(beta, N, k, n, h_exp=-30)
+        assert abs(g - fd) / abs(g) < mpm.mpf(10) ** -50
+
+
+def test_gradient_rational_beta_vs_finite_difference():
+    """beta = 9/20: the analytic gradient (digamma at x = 20(s+1)/9 through
+    the recurrence and Gauss's theorem) against the central difference of
+    the whole pipeline with mpmath's Gamma at beta +- 1e-30."""
+    n, N, k = 16, 8, 4
+    beta = Fraction(9, 20)
+    with mpm.workprec(32 * n + 128):
+        mu = M.gamma_moments(mpm.mpf(9) / 20, N, n)
+    D, L = LD.ldlt(mu, N, n)
+    X = IB.partial_inverse(L, N, k, n)
+    with mpm.workprec(1200):
+        g, _, _ = GR.analytic_grad(beta, lambda s: mpm.gamma(mpm.mpf(20 * (s + 1)) / 9) * 20 / 9, L, D, X, k, n)
         fd = GR.fd_grad(beta, N, k, n, h_exp=-30)
         assert abs(g - fd) / abs(g) < mpm.mpf(10) ** -50
