@@ -141,9 +141,20 @@ HK_API hk_status hk_inv_block(hk_ctx* ctx, int k);
  * (Sec. 4.2), with the truncation estimate lambda_m(k) - lambda_m(k-1) from the
  * leading (k-1) x (k-1) block (Sec. 4.5, Table 2).  Outputs (host, any may be
  * NULL): lambda in the number layout (n_eig numbers), lambda_f64[n_eig],
- * trunc_err_f64[n_eig] (NaN when k == 1).  Synchronises. */
+ * trunc_err_f64[n_eig] (NaN when k == 1).  Synchronises.  Returns
+ * HK_ERR_PRECISION (nothing written) when the working precision is below the
+ * min_bits of hk_precision_loss. */
 HK_API hk_status hk_lambda1(hk_ctx* ctx, int n_eig, int32_t* sign, int32_t* exp, uint32_t* limbs,
                             double* lambda_f64, double* trunc_err_f64);
+
+/* Precision check of the factorisation (Sec. 4.3 leaves the working
+ * precision to the user; Sec. 4.1 confirms it by doubling).  loss_bits =
+ * max(0, max_i ceil(log2(mu_{2i} / d_i))): the leading bits that cancelled in
+ * the pivots, formed on the device right after hk_ldlt.  min_bits =
+ * ceil(1.8 loss + 197): 133 bits for 1e-40 and 64 to spare, 1.8 bounding the
+ * ratio of the loss precision doubling shows to this estimate (about 1.7 at
+ * beta = 1/2).  After hk_ldlt; outputs (host) may be NULL; synchronises. */
+HK_API hk_status hk_precision_loss(hk_ctx* ctx, int32_t* loss_bits, int32_t* min_bits);
 
 /* a8. d lambda_1 / d beta of the block estimate lambda_1 = 1/nu_1:
  * (w^T Hdot w)/nu_1^2 with w = L^{-T} D^{-1} X u (u the unit eigenvector) and

@@ -465,6 +465,37 @@ hk_status hk_set_moments(hk_ctx* h, int N, int bits, const int32_t* sign, const 
   return HK_OK;
 }
 
+// Loss estimate of the factorisation: max(0, max_i ceil(log2(mu_{2i}/d_i)))
+// over the pivots d_i = A[i][i].  Each pivot is what is left of its diagonal
+// moment after the eliminations (Sec. 4.3), so the ratio counts the leading
+// bits that cancelled.  One thread per pivot, into *out (cleared before);
+// non-positive pivots are left to the ERR_NOT_PD flag.
+__global__ void k_loss_estimate(MPVec MU, MPVec A, int N, int n, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t pd = tri_pos(N, i, i);
+  const uint32_t* d = A.mant + pd * n;
+  const uint32_t* m = MU.mant + (int64_t)(2 * i) * n;
+  if (A.sgn[pd] || d[n - 1] == 0u || m[n - 1] == 0u) return;
+  // the top two limbs give log2 of each to far better than a bit
+  const double td = (double)d[n - 1] + (double)d[n - 2] * 0x1p-32;
+  const double tm = (double)m[n - 1] + (double)m[n - 2] * 0x1p-32;
+  const double l = 32.0 * ((double)MU.exp[2 * i] - (double)A.exp[pd]) + log2(tm) - log2(td);
+  const int v = (int)ceil(l);
+  if (v > 0) atomicMax(out, v);
+}
+
+// The rule on the loss estimate: a result keeps 133 bits (1e-40) and 64 to
+// spare when bits - 1.8 loss >= 197; 1.8 bounds the ratio of the loss seen
+// by precision doubling to the estimate (about 1.7 at beta = 1/2).
+static int min_bits_for(int loss) { return (int)std::ceil(1.8 * loss + 197.0 - 1e-9); }
+
+static hk_status read_loss(Ctx& c, int& loss) {
+  hk_status st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising");
+  if (st != HK_OK) return st;
+  return check_cuda(c, cudaMemcpy(&loss, c.d_err + 1, sizeof(int), cudaMemcpyDeviceToHost), "reading the loss");
+}
+
 hk_status hk_ldlt(hk_ctx* h) {
   hk_status st = enter(h);
   if (st != HK_OK) return st;
@@ -472,9 +503,26 @@ hk_status hk_ldlt(hk_ctx* h) {
   if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_ldlt before the moments");
   const size_t pe0 = c.prof ? prof_mark(c) : 0;
   st = ops_for(c.M)->ldlt(c);
+  if (st == HK_OK && (st = check_cuda(c, cudaMemsetAsync(c.d_err + 1, 0, sizeof(int), c.stream), "clearing")) == HK_OK) {
+    k_loss_estimate<<<(c.N + 127) / 128, 128, 0, c.stream>>>(c.mu.view(), c.A.view(), c.N, c.n, c.d_err + 1);
+    count_launch(c);
+    st = check_cuda(c, cudaGetLastError(), "k_loss_estimate");
+  }
   if (c.prof) c.stage_ev.push_back({1, {pe0, prof_mark(c)}});
   if (st == HK_OK) c.stage = ST_LDLT;
   return st;
+}
+
+hk_status hk_precision_loss(hk_ctx* h, int32_t* loss_bits, int32_t* min_bits) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (c.stage < ST_LDLT) return set_error(c, HK_ERR_ORDER, "hk_precision_loss before hk_ldlt");
+  int loss = 0;
+  if ((st = read_loss(c, loss)) != HK_OK) return st;
+  if (loss_bits) *loss_bits = loss;
+  if (min_bits) *min_bits = min_bits_for(loss);
+  return HK_OK;
 }
 
 hk_status hk_inv_block(hk_ctx* h, int k) {
@@ -502,6 +550,15 @@ hk_status hk_lambda1(hk_ctx* h, int n_eig, int32_t* sign, int32_t* exp, uint32_t
   if ((st = ops_for(c.M)->lambda(c, n_eig)) != HK_OK) return st;
   if (c.prof) c.stage_ev.push_back({3, {pe0, prof_mark(c)}});
   if ((st = read_device_flags(c)) != HK_OK) return st;
+  int loss = 0;
+  if ((st = read_loss(c, loss)) != HK_OK) return st;
+  if (32 * c.n < min_bits_for(loss)) {
+    char msg[192];
+    std::snprintf(msg, sizeof(msg),
+                  "estimated loss of %d bits leaves fewer than 133 + 64 of the %d: use at least %d bits", loss,
+                  32 * c.n, min_bits_for(loss));
+    return set_error(c, HK_ERR_PRECISION, msg);
+  }
   for (int m = 0; m < n_eig; ++m) {
     if (sign) sign[m] = c.lam_sgn[m];
     if (exp) exp[m] = c.lam_exp[m];

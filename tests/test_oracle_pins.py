@@ -23,6 +23,7 @@ from oracle import eigen as EG
 from oracle import exact as EX
 from oracle import grad as GR
 from oracle import pipeline as PL
+from oracle import precision as PR
 from tests import inputs
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -293,3 +294,28 @@ def test_gradient_rational_beta_vs_finite_difference():
         g, _, _ = GR.analytic_grad(beta, lambda s: mpm.gamma(mpm.mpf(20 * (s + 1)) / 9) * 20 / 9, L, D, X, k, n)
         fd = GR.fd_grad(beta, N, k, n, h_exp=-30)
         assert abs(g - fd) / abs(g) < mpm.mpf(10) ** -50
+
+
+def test_loss_estimate_closed_form_beta1():
+    """beta = 1: d_i = (i!)^2 and mu_{2i} = (2i)!, so mu_{2i}/d_i = C(2i, i),
+    largest at i = N - 1: the loss estimate is ceil(log2 C(2N-2, N-1))."""
+    from math import comb
+    assert [PR.ceil_log2(Fraction(v)) for v in (1, 2, 3, 4, 5)] == [0, 1, 2, 2, 3]
+    assert PR.ceil_log2(Fraction(1, 3)) == -1 and PR.ceil_log2(Fraction(1, 4)) == -2
+    N, n = 40, 64
+    mu = M.moments(Fraction(1), N, n)
+    D, _ = LD.ldlt(mu, N, n)
+    assert PR.loss_estimate(mu, D) == PR.ceil_log2(Fraction(comb(2 * N - 2, N - 1)))
+    assert PR.min_bits(0) == 197 and PR.min_bits(10) == 215 and PR.min_bits(11) == 217
+
+
+def test_loss_estimate_truncated_equals_exact():
+    """beta = 1/2, N = 14: the estimate from the truncated factor at 512 bits
+    equals the one from the exact rational factor of H_N."""
+    N = 14
+    mu_q = [2 * factorial(2 * j + 1) for j in range(2 * N - 1)]
+    Dq, _ = EX.ldlt_exact([[mu_q[i + j] for j in range(N)] for i in range(N)])
+    want = max(0, max(PR.ceil_log2(Fraction(mu_q[2 * i]) / Dq[i]) for i in range(N)))
+    mu = M.moments(Fraction(1, 2), N, 16)
+    D, _ = LD.ldlt(mu, N, 16)
+    assert PR.loss_estimate(mu, D) == want
