@@ -76,8 +76,9 @@ def parse():
     ap.add_argument("--profile-case", action="store_true",
                     help="only run moments + LDL^T once at --N/--bits (a small case for ncu captures)")
     ap.add_argument("--rows", default="",
-                    help="table2: comma-separated N values of Table 2 to run (default: all nine)")
-    ap.add_argument("--workload", default="single", choices=["single", "batch", "table2"],
+                    help="table2 / regimes: comma-separated N values to run (default: all nine rows of "
+                         "Table 2 / 128,256,512,1024)")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "table2", "regimes"],
                     help="batch: 16 uneven instances (beta = 1/m, m in 1..4, N in {128..384}, k = 16, "
                          "32 N bits) through hk_batch_run, beside the same instances one by one")
     return ap.parse_args()
@@ -451,10 +452,67 @@ def run_table2(a):
                               paper=table["fit"])), flush=True)
 
 
+def local_slopes(pts, xf):
+    """Slopes of log lambda between successive (N, lambda) points against xf(N)."""
+    import math
+    return [(math.log(l1) - math.log(l0)) / (xf(n1) - xf(n0)) for (n0, l0), (n1, l1) in zip(pts, pts[1:])]
+
+
+def run_regimes(a):
+    """The three regimes of the weight exp(-x^beta) (abstract, Sec. 1 and 6):
+    lambda_1 bounded below for beta < 1/2 (indeterminate moment problem),
+    algebraic decay at beta = 1/2, exponential decay for beta > 1/2; shown at
+    beta = 1/3, 1/2, 1 (exact moments) for N = 128 ... 1024, k = 64 (at
+    beta = 1 and N = 1024 a k = 32 block still has a 30 % truncation
+    estimate; k = 64 brings every row below 1e-20).  Each
+    solve runs at the least compiled width the precision check accepts
+    (hk_precision_loss, tried from a width of 2 N + 197 bits up).  One JSON
+    line per solve, then one per beta with the local slopes of log lambda_1
+    against log N and against sqrt(N)."""
+    import math
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_1810_01478_gb300 as hk
+    widths = sorted(hk.hk_supported_bits())
+    Ns = [int(x) for x in a.rows.split(",") if x] if a.rows else [128, 256, 512, 1024]
+    for m in (3, 2, 1):
+        pts = []
+        for N in Ns:
+            k = min(64, N)
+            bits = next((w for w in widths if w >= 2 * N + 197), widths[-1])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            while True:
+                h = hk.Hankel(0)
+                try:
+                    h.moments(1, m, N, bits)
+                    h.ldlt()
+                    loss, need = h.precision_loss()
+                    if need > bits and bits < widths[-1]:
+                        bits = next((w for w in widths if w >= need), widths[-1])
+                        continue
+                    h.inv_block(k)
+                    _, _, _, lam, terr = h.lambda1(3)
+                    break
+                finally:
+                    h.close()
+            dt = time.perf_counter() - t0
+            pts.append((N, float(lam[0])))
+            print(json.dumps(dict(workload="regimes", beta=f"1/{m}", N=N, k=k, bits=bits, loss_bits=loss,
+                                  seconds=dt, lambda_f64=[float(v) for v in lam],
+                                  trunc_err_f64=[float(v) for v in terr])), flush=True)
+        print(json.dumps(dict(workload="regimes_slopes", beta=f"1/{m}", N=Ns,
+                              dlog_lambda_dlog_N=local_slopes(pts, math.log),
+                              dlog_lambda_dsqrt_N=local_slopes(pts, math.sqrt))), flush=True)
+
+
 if __name__ == "__main__":
     args = parse()
     if args.workload == "table2":
         run_table2(args)
+    elif args.workload == "regimes":
+        run_regimes(args)
     elif args.workload == "batch":
         run_batch(args)
     elif args.profile_case:

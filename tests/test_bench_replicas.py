@@ -60,3 +60,14 @@ def test_reference_arm_prints_on_rank_zero_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_local_slopes_of_the_regimes_workload():
+    """bench.local_slopes: a power law N^-a has log-log slope -a, and
+    exp(-c sqrt N) has slope -c against sqrt N, between every pair."""
+    import math
+    import bench
+    pts = [(n, n ** -0.6366) for n in (128, 256, 512, 1024)]
+    assert all(abs(s + 0.6366) < 1e-12 for s in bench.local_slopes(pts, math.log))
+    pts = [(n, math.exp(-3.5 * math.sqrt(n))) for n in (100, 400, 900)]
+    assert all(abs(s + 3.5) < 1e-9 for s in bench.local_slopes(pts, math.sqrt))
