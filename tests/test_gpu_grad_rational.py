@@ -4,7 +4,8 @@ r = 1..a-1, by the recurrence psi(x + 1) = psi(x) + 1/x (Sec. 4.2's
 moments differentiated in beta).  Compared with the oracle's analytic
 gradient (oracle.grad.analytic_grad: mpmath's digamma at every x, mpmath's
 Gamma for mu) on the factor of the same moments, to 1e-40, at a schoolbook
-width (2048 bits) and at an NTT width (8192 bits); the psi constants are
+width (2048 bits) and at an NTT width (8192 bits), and at beta = 11/20
+(ten constants) with N = 64, k = 16, 4096 bits; the psi constants are
 handed over wider and narrower than the working width.  The oracle's psi
 at rational points is Gauss's digamma theorem after the same recurrence
 (pinned against mpmath.digamma on the CPU), and its mu are the oracle's
@@ -40,10 +41,10 @@ def psi_constants(a, nc):
     return to_arrays(out, nc)
 
 
-@pytest.mark.parametrize("bits,dn", [(2048, 4), (8192, -2)])
-def test_grad_rational_beta_vs_oracle(bits, dn):
+@pytest.mark.parametrize("beta,N,k,bits,dn", [(Fraction(9, 20), 40, 8, 2048, 4), (Fraction(9, 20), 40, 8, 8192, -2),
+                                               (Fraction(11, 20), 64, 16, 4096, 0)])
+def test_grad_rational_beta_vs_oracle(beta, N, k, bits, dn):
     import paper_1810_01478_gb300 as hk
-    beta, N, k = Fraction(9, 20), 40, 8
     n = bits // 32
     a, b = beta.numerator, beta.denominator
     consts = constants(beta)
