@@ -270,7 +270,17 @@ def run_ours(a):
     props = torch.cuda.get_device_properties(local)
     sms = props.multi_processor_count
     sm_max = (clk or {}).get("sm_max_mhz") or 2070.0
-    peak_sb = sms * IMAD_PER_CLK_PER_SM / IMAD_PER_LIMB_MAC * sm_max * 1e6 / 1e12  # T limb-MAC/s
+    # the integer pipe's measured rates (operations per SM clock), after the timed region
+    try:
+        rate_imad, rate_mod = hk.hk_alu_peak(local, 0), hk.hk_alu_peak(local, 1)
+        # an SM issues at most 128 thread instructions per clock; a modular
+        # multiplication takes three multiplies: anything else is not a rate
+        if not (0 < rate_mod <= rate_imad <= 128):
+            rate_imad = rate_mod = None
+    except (RuntimeError, AttributeError):
+        rate_imad = rate_mod = None
+    derived_sb = sms * IMAD_PER_CLK_PER_SM / IMAD_PER_LIMB_MAC * sm_max * 1e6 / 1e12  # T limb-MAC/s
+    peak_sb = sms * rate_imad / IMAD_PER_LIMB_MAC * sm_max * 1e6 / 1e12 if rate_imad else derived_sb
     avg_launch_ms = prof["trailing_ms"] / max(prof["trailing_launches"], 1)
     macs_per_launch = prof["trailing_limb_macs"] / max(prof["trailing_launches"], 1)
     updates_per_launch = macs_per_launch / (n * n)
@@ -286,20 +296,26 @@ def run_ours(a):
                 issue = t.get("issue_active_frac")
         except (ValueError, KeyError):
             traffic = issue = None
+    sb_rate = (f"{rate_imad:.1f} IMAD/clk measured (hk_alu_peak: mad.lo.u32 chains, one 1024-thread block "
+               f"per SM, clock64)" if rate_imad else f"{IMAD_PER_CLK_PER_SM} IMAD/clk (derived)")
     schoolbook = dict(achieved=achieved_sb, peak=peak_sb, unit="Tlimb-MAC/s", frac=achieved_sb / peak_sb,
+                      derived_peak=derived_sb,
                       note=f"n^2 = {n * n} limb products per update (the schoolbook-equivalent convention); "
-                           f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_LIMB_MAC} IMAD per limb "
-                           f"product x {sm_max:.0f} MHz (derived)")
+                           f"{sms} SMs x {sb_rate} / {IMAD_PER_LIMB_MAC} IMAD per limb product x {sm_max:.0f} MHz")
     if ntt:
         mm = ntt_modmuls_per_update(n)
-        peak = sms * IMAD_PER_CLK_PER_SM / IMAD_PER_MODMUL * sm_max * 1e6 / 1e12
+        derived = sms * IMAD_PER_CLK_PER_SM / IMAD_PER_MODMUL * sm_max * 1e6 / 1e12
+        peak = sms * rate_mod * sm_max * 1e6 / 1e12 if rate_mod else derived
         achieved = mm * updates_per_launch / (avg_launch_ms / 1e3) / 1e12
+        mod_rate = (f"{rate_mod:.2f} modular multiplications/clk measured (hk_alu_peak: lazy Shoup chains, one "
+                    f"1024-thread block per SM, clock64)" if rate_mod else
+                    f"{IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_MODMUL} IMAD per modular multiplication (derived)")
         roofline = dict(bound="alu", achieved=achieved, peak=peak, unit="Tmodmul/s", frac=achieved / peak,
                         traffic=traffic, kernel="k_trailing_ntt (Algorithm 1 trailing update, NTT products)",
                         work_per_update=f"{mm} modular multiplications (3 primes, length {ntt_shape(n)[0]} x "
                                         f"{ntt_shape(n)[1]})",
-                        peak_note=f"{sms} SMs x {IMAD_PER_CLK_PER_SM} IMAD/clk / {IMAD_PER_MODMUL} IMAD per "
-                                  f"modular multiplication x {sm_max:.0f} MHz (derived, not measured)",
+                        peak_note=f"{sms} SMs x {mod_rate} x {sm_max:.0f} MHz",
+                        derived_peak=derived,
                         issue_active_frac=issue,
                         issue_note="fraction of cycles the kernel issues an instruction (ncu capture of the same "
                                    "kernel source, profiles/trailing_traffic.json): the bound it actually meets",

@@ -147,6 +147,15 @@ HK_API hk_status hk_inv_block(hk_ctx* ctx, int k);
 HK_API hk_status hk_lambda1(hk_ctx* ctx, int n_eig, int32_t* sign, int32_t* exp, uint32_t* limbs,
                             double* lambda_f64, double* trunc_err_f64);
 
+/* Measured throughput of the integer multiply pipe that the exact products
+ * run on, for the rooflines: operations per SM clock from a microbenchmark
+ * (one 1024-thread block per SM, 8 independent chains per thread, the
+ * block's own clock count, median over SMs).  kind 0: 32-bit multiply-add
+ * (mad.lo.u32, x = x x + c); kind 1: the lazy Shoup modular multiplication the transforms
+ * use (x w - hi(x w') p).  Runs two launches of a few ms on `device`'s
+ * default stream and synchronises the device. */
+HK_API hk_status hk_alu_peak(int device, int kind, double* per_clk_per_sm);
+
 /* Precision check of the factorisation (Sec. 4.3 leaves the working
  * precision to the user; Sec. 4.1 confirms it by doubling).  loss_bits =
  * max(0, max_i ceil(log2(mu_{2i} / d_i))): the leading bits that cancelled in

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
            "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
            "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run",
-           "hk_set_product_algorithm", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss"]
+           "hk_set_product_algorithm", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"]
 HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT = 0, 1, 2
 HK_NTT_AUTO_MIN_M = 8  # include/hk.h: AUTO uses NTT products from 32 * 8 limbs (8192 bits)
 
@@ -81,6 +81,7 @@ def load(path=LIB_PATH):
                                    _I32P, _U32P]
     L.hk_set_psi_constants.argtypes = [_P, ctypes.c_int, ctypes.c_int, _I32P, _I32P, _U32P]
     L.hk_precision_loss.argtypes = [_P, _I32P, _I32P]
+    L.hk_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.hk_ldlt.argtypes = [_P]
     L.hk_inv_block.argtypes = [_P, ctypes.c_int]
     L.hk_lambda1.argtypes = [_P, ctypes.c_int, _I32P, _I32P, _U32P, _F64P, _F64P]
@@ -94,7 +95,7 @@ def load(path=LIB_PATH):
     L.hk_ldlt_noalloc.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 6 + [_P]
     L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
     for name in ("hk_set_product_algorithm", "hk_batch_run", "hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
-                 "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss"):
+                 "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -146,6 +147,14 @@ def hk_moments_gamma(ctx, beta_num, beta_den, N, bits, c_exp, c_limbs):
     nc = c_limbs.shape[1] if c_limbs.ndim == 2 and c_limbs.shape[0] else 1
     _check(load().hk_moments_gamma(ctx, beta_num, beta_den, N, bits, nc, _ptr(c_exp, ctypes.c_int32),
                                    _ptr(c_limbs, ctypes.c_uint32)), ctx)
+
+
+def hk_alu_peak(device, kind):
+    """Measured operations per SM clock of the integer multiply pipe:
+    kind 0 = mad.lo.u32, kind 1 = lazy Shoup modular multiplication."""
+    v = ctypes.c_double(0.0)
+    _check(load().hk_alu_peak(device, kind, ctypes.byref(v)), None, "hk_alu_peak")
+    return v.value
 
 
 def hk_precision_loss(ctx):

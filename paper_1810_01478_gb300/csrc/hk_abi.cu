@@ -1,5 +1,6 @@
 // The C ABI of libhk (declared in include/hk.h): context management, call-order
 // enforcement, host <-> device transfers and dispatch to the per-width launchers.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <chrono>
@@ -226,6 +227,61 @@ static hk_status enter(hk_ctx* h) {
   if (!h) return HK_ERR_ARG;
   if (h->c.sticky != HK_OK) return h->c.sticky;
   return check_cuda(h->c, cudaSetDevice(h->c.device), "cudaSetDevice");
+}
+
+// Loss estimate of the factorisation: max(0, max_i ceil(log2(mu_{2i}/d_i)))
+// over the pivots d_i = A[i][i].  Each pivot is what is left of its diagonal
+// moment after the eliminations (Sec. 4.3), so the ratio counts the leading
+// bits that cancelled.  One thread per pivot, into *out (cleared before);
+// non-positive pivots are left to the ERR_NOT_PD flag.
+__global__ void k_loss_estimate(MPVec MU, MPVec A, int N, int n, int* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int64_t pd = tri_pos(N, i, i);
+  const uint32_t* d = A.mant + pd * n;
+  const uint32_t* m = MU.mant + (int64_t)(2 * i) * n;
+  if (A.sgn[pd] || d[n - 1] == 0u || m[n - 1] == 0u) return;
+  // the top two limbs give log2 of each to far better than a bit
+  const double td = (double)d[n - 1] + (double)d[n - 2] * 0x1p-32;
+  const double tm = (double)m[n - 1] + (double)m[n - 2] * 0x1p-32;
+  const double l = 32.0 * ((double)MU.exp[2 * i] - (double)A.exp[pd]) + log2(tm) - log2(td);
+  const int v = (int)ceil(l);
+  if (v > 0) atomicMax(out, v);
+}
+
+// Throughput of the integer multiply pipe, in operations per SM clock: one
+// block of kPeakThreads per SM (its dynamic shared memory keeps a second
+// block off the SM), kPeakChains independent chains per thread, the block's
+// clock64 span.  KIND 0: mad.lo.u32 (x = x x + c; an affine step would let
+// the compiler merge unrolled steps into one); KIND 1: the lazy Shoup
+// modular multiplication of the transforms (x w - hi(x w') p).
+constexpr int kPeakThreads = 1024, kPeakChains = 8, kPeakIters = 1 << 14;
+constexpr int kPeakSmem = 160 * 1024;
+
+template <int KIND>
+__global__ void __launch_bounds__(1024, 1) k_alu_peak(int iters, uint32_t seed, long long* span, uint32_t* sink) {
+  uint32_t x[kPeakChains];
+#pragma unroll
+  for (int j = 0; j < kPeakChains; ++j) x[j] = seed + threadIdx.x * kPeakChains + j;
+  const uint32_t p = 1073707009u, w = 0x2A3B4C5Du % 1073707009u;
+  const uint32_t ws = (uint32_t)(((uint64_t)w << 32) / p);
+  __syncthreads();
+  const long long t0 = clock64();
+#pragma unroll 4
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int j = 0; j < kPeakChains; ++j) {
+      if constexpr (KIND == 0) x[j] = x[j] * x[j] + (0x7F4A7C15u + j);  // not affine: no folding of steps
+      else x[j] = mul_shoup_lazy(x[j], w, ws, p);
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  uint32_t acc = 0;
+#pragma unroll
+  for (int j = 0; j < kPeakChains; ++j) acc ^= x[j];
+  if (acc == 0x5A5A5A5Au) sink[threadIdx.x & 15] = acc;  // keeps the chains live
+  if (threadIdx.x == 0) span[blockIdx.x] = t1 - t0;
 }
 
 extern "C" {
@@ -465,26 +521,6 @@ hk_status hk_set_moments(hk_ctx* h, int N, int bits, const int32_t* sign, const 
   return HK_OK;
 }
 
-// Loss estimate of the factorisation: max(0, max_i ceil(log2(mu_{2i}/d_i)))
-// over the pivots d_i = A[i][i].  Each pivot is what is left of its diagonal
-// moment after the eliminations (Sec. 4.3), so the ratio counts the leading
-// bits that cancelled.  One thread per pivot, into *out (cleared before);
-// non-positive pivots are left to the ERR_NOT_PD flag.
-__global__ void k_loss_estimate(MPVec MU, MPVec A, int N, int n, int* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int64_t pd = tri_pos(N, i, i);
-  const uint32_t* d = A.mant + pd * n;
-  const uint32_t* m = MU.mant + (int64_t)(2 * i) * n;
-  if (A.sgn[pd] || d[n - 1] == 0u || m[n - 1] == 0u) return;
-  // the top two limbs give log2 of each to far better than a bit
-  const double td = (double)d[n - 1] + (double)d[n - 2] * 0x1p-32;
-  const double tm = (double)m[n - 1] + (double)m[n - 2] * 0x1p-32;
-  const double l = 32.0 * ((double)MU.exp[2 * i] - (double)A.exp[pd]) + log2(tm) - log2(td);
-  const int v = (int)ceil(l);
-  if (v > 0) atomicMax(out, v);
-}
-
 // The rule on the loss estimate: a result keeps 133 bits (1e-40) and 64 to
 // spare when bits - 1.8 loss >= 197; 1.8 bounds the ratio of the loss seen
 // by precision doubling to the estimate (about 1.7 at beta = 1/2).
@@ -511,6 +547,40 @@ hk_status hk_ldlt(hk_ctx* h) {
   if (c.prof) c.stage_ev.push_back({1, {pe0, prof_mark(c)}});
   if (st == HK_OK) c.stage = ST_LDLT;
   return st;
+}
+
+hk_status hk_alu_peak(int device, int kind, double* per_clk_per_sm) {
+  if (kind < 0 || kind > 1 || !per_clk_per_sm) return HK_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return HK_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms < 1)
+    return HK_ERR_CUDA;
+  auto kern = kind == 0 ? k_alu_peak<0> : k_alu_peak<1>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakSmem) != cudaSuccess)
+    return HK_ERR_CUDA;
+  long long* span = nullptr;
+  uint32_t* sink = nullptr;
+  if (cudaMalloc(&span, sizeof(long long) * sms) != cudaSuccess) return HK_ERR_NOMEM;
+  if (cudaMalloc(&sink, 64) != cudaSuccess) {
+    cudaFree(span);
+    return HK_ERR_NOMEM;
+  }
+  std::vector<long long> h(sms);
+  cudaError_t e = cudaSuccess;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    kern<<<sms, kPeakThreads, kPeakSmem>>>(kPeakIters, 0x2545F491u + rep, span, sink);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(h.data(), span, sizeof(long long) * sms, cudaMemcpyDeviceToHost);
+  cudaFree(span);
+  cudaFree(sink);
+  if (e != cudaSuccess) return HK_ERR_CUDA;
+  std::sort(h.begin(), h.end());
+  const double med = (double)h[sms / 2];
+  if (med <= 0) return HK_ERR_CUDA;
+  *per_clk_per_sm = (double)kPeakThreads * kPeakChains * (double)kPeakIters / med;
+  return HK_OK;
 }
 
 hk_status hk_precision_loss(hk_ctx* h, int32_t* loss_bits, int32_t* min_bits) {
