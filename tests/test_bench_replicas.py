@@ -71,3 +71,29 @@ def test_local_slopes_of_the_regimes_workload():
     assert all(abs(s + 0.6366) < 1e-12 for s in bench.local_slopes(pts, math.log))
     pts = [(n, math.exp(-3.5 * math.sqrt(n))) for n in (100, 400, 900)]
     assert all(abs(s + 3.5) < 1e-9 for s in bench.local_slopes(pts, math.sqrt))
+
+
+def test_trailing_roofline_arithmetic():
+    """bench.trailing_roofline: achieved = work per launch / average launch
+    time against 152 SMs x 64 IMAD/clk / 4 slots per modular multiplication x
+    the clock; measured rates are kept only when physical."""
+    import bench
+    n, per_launch, launches, ms = 768, 1000, 2, 10.0
+    prof = dict(trailing_launches=launches, trailing_ms=ms, trailing_limb_macs=launches * per_launch * n * n)
+    r = bench.trailing_roofline(prof, n, True, 152, 2070.0, (63.8, 16.0), 6807.3, 0.52)
+    mm = bench.ntt_modmuls_per_update(n)
+    assert mm == 31488
+    want = mm * per_launch / (ms / launches / 1e3) / 1e12
+    assert abs(r["achieved"] - want) < 1e-12 * want
+    assert abs(r["peak"] - 152 * 16 * 2070e6 / 1e12) < 1e-9
+    assert abs(r["frac"] - want / r["peak"]) < 1e-12
+    assert abs(r["traffic"] - 6807.3 * per_launch) < 1e-6
+    assert r["measured_rates"]["modmul_per_clk_sm"] == 16.0 and r["issue_active_frac"] == 0.52
+    sb = r["schoolbook_equiv"]
+    assert abs(sb["peak"] - 152 * 32 * 2070e6 / 1e12) < 1e-9
+    assert abs(sb["achieved"] - per_launch * n * n / (ms / launches / 1e3) / 1e12) < 1e-9
+    # a rate above the issue limit is not a rate; no traffic capture gives null
+    r = bench.trailing_roofline(prof, n, True, 152, 2070.0, (252.8, 16.0), None, None)
+    assert r["measured_rates"] is None and r["traffic"] is None
+    r = bench.trailing_roofline(prof, 128, False, 152, 2070.0, None, None, None)
+    assert r["unit"] == "Tlimb-MAC/s" and r["measured_rates"] is None
