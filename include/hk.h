@@ -22,8 +22,10 @@
  * elementwise primitives are owned by the caller.
  *
  * Streams.  Every call is ordered on the cudaStream_t given to hk_create
- * (borrowed, never destroyed).  hk_lambda1, hk_lambda1_grad and hk_export
- * synchronise that stream; the other calls only enqueue work.  Internally the
+ * (borrowed, never destroyed).  hk_lambda1, hk_lambda1_grad, hk_export and
+ * hk_precision_loss synchronise that stream; hk_set_moments and
+ * hk_set_psi_constants wait for their host-to-device copies; the other
+ * calls only enqueue work.  Internally the
  * LDL^T at NTT widths runs on high-priority streams of the context, forked
  * from and joined back to that stream, and hk_inv_block runs Algorithm 4 on a
  * low-priority stream beside the still-running factorisation (each step
