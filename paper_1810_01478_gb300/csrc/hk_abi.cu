@@ -245,7 +245,7 @@ __global__ void k_loss_estimate(MPVec MU, MPVec A, int N, int n, int* out) {
   const double td = (double)d[n - 1] + (double)d[n - 2] * 0x1p-32;
   const double tm = (double)m[n - 1] + (double)m[n - 2] * 0x1p-32;
   const double l = 32.0 * ((double)MU.exp[2 * i] - (double)A.exp[pd]) + log2(tm) - log2(td);
-  const int v = (int)ceil(l);
+  const int v = (int)ceil(fmin(l, 1.0e9));  // imported moments may carry any exponents
   if (v > 0) atomicMax(out, v);
 }
 
@@ -524,7 +524,7 @@ hk_status hk_set_moments(hk_ctx* h, int N, int bits, const int32_t* sign, const 
 // The rule on the loss estimate: a result keeps 133 bits (1e-40) and 64 to
 // spare when bits - 1.8 loss >= 197; 1.8 bounds the ratio of the loss seen
 // by precision doubling to the estimate (about 1.7 at beta = 1/2).
-static int min_bits_for(int loss) { return (int)std::ceil(1.8 * loss + 197.0 - 1e-9); }
+static int min_bits_for(int loss) { return (int)std::ceil(std::min(1.8 * loss + 197.0, 2.0e9) - 1e-9); }
 
 static hk_status read_loss(Ctx& c, int& loss) {
   hk_status st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising");
