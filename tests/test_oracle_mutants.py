@@ -8,8 +8,10 @@ quotient through a rounded reciprocal, round-to-nearest instead of
 truncation, an off-by-one moment index, a pivot that misses its updates,
 Algorithm 4 without the negated column or without its last term, the block
 without 1/D, the smallest eigenvalue instead of the largest, a sign error in
-Gauss's digamma theorem, a gradient with the wrong sign of psi, and a floor
-where the loss estimate takes a ceiling."""
+Gauss's digamma theorem, a gradient with the wrong sign of psi, a floor
+where the loss estimate takes a ceiling, a harmonic number one index too
+far, a missing 1/a in the Gamma-constant route to the moments, and the loss
+estimate against mu_i instead of mu_2i."""
 from fractions import Fraction
 from math import factorial
 
@@ -160,4 +162,46 @@ def test_loss_estimate_floor(monkeypatch):
             t += 1
         return t
     monkeypatch.setattr(PR, "ceil_log2", floor_log2)
+    assert caught(TP.test_loss_estimate_closed_form_beta1)
+
+
+def test_harmonic_index_off_by_one(monkeypatch):
+    orig = GR.psi
+
+    def psi_h(x, mp):
+        v = orig(x, mp)
+        if isinstance(x, int) or (isinstance(x, Fraction) and x.denominator == 1):
+            v += mp.mpf(1) / int(x)                          # H_x instead of H_{x-1}
+        return v
+    monkeypatch.setattr(GR, "psi", psi_h)
+    assert caught(TP.test_psi_integer_identity_matches_digamma)
+
+
+def test_gamma_route_missing_factor(monkeypatch):
+    def moments_wrong(beta, N, n, consts):
+        beta = Fraction(beta)
+        a, b = beta.numerator, beta.denominator
+        mus = []
+        for j in range(2 * N - 1):
+            q, r = divmod(b * (j + 1), a)
+            if r == 0:
+                v = Fraction(b, a) * factorial(q - 1)
+            else:
+                num = b
+                for i in range(q):
+                    num *= r + i * a
+                v = Fraction(num, a ** q) * consts[r]          # a^q for a^(q+1)
+            mus.append(F.from_fraction(v, n))
+        return mus
+    monkeypatch.setattr(M, "moments_from_constants", moments_wrong)
+    assert caught(TP.test_rational_beta_moments_from_constants)
+
+
+def test_loss_estimate_wrong_moment(monkeypatch):
+    def loss_wrong(mu, D):
+        best = 0
+        for i, d in enumerate(D):
+            best = max(best, PR.ceil_log2(F.to_fraction(mu[i]) / F.to_fraction(d)))   # mu_i for mu_2i
+        return best
+    monkeypatch.setattr(PR, "loss_estimate", loss_wrong)
     assert caught(TP.test_loss_estimate_closed_form_beta1)
