@@ -517,11 +517,12 @@ struct Tail {
         den[v] = v > a ? v - a : 1;
       }
       if ((st = small(c, num, den, H0->view())) != HK_OK) return st;
+      // (only the v <= V that exist: beta > 2N - 1 leaves some seeds unused)
       std::vector<ChainTask> seeds;
-      for (int64_t r = 1; r < a; ++r) seeds.push_back(ChainTask{r, r - 1, 0, 0, 0, 0, 0, 0});
+      for (int64_t r = 1; r < a && r <= V; ++r) seeds.push_back(ChainTask{r, r - 1, 0, 0, 0, 0, 0, 0});
       if ((st = chains(c, seeds, ONE->view(), ONE->view(), c.psi.view(), H0->view())) != HK_OK) return st;
-      if ((st = chains(c, {ChainTask{a, 1, 0, 0, 0, 0, 0, CH_NEG_INIT}}, ONE->view(), ONE->view(), cst->view(),
-                       H0->view())) != HK_OK)
+      if (a <= V && (st = chains(c, {ChainTask{a, 1, 0, 0, 0, 0, 0, CH_NEG_INIT}}, ONE->view(), ONE->view(),
+                                 cst->view(), H0->view())) != HK_OK)
         return st;
     }
     for (int64_t d = a; d <= V; d <<= 1) {
