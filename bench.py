@@ -489,7 +489,7 @@ def run_regimes(a):
     beta = 1 and N = 1024 a k = 32 block still has a 30 % truncation
     estimate; k = 64 brings every row below 1e-20).  Each
     solve runs at the least compiled width the precision check accepts
-    (hk_precision_loss, tried from a width of 2 N + 197 bits up).  One JSON
+    (hk_precision_loss, tried from a width of 2 N + 229 bits up).  One JSON
     line per solve, then one per beta with the local slopes of log lambda_1
     against log N and against sqrt(N)."""
     import math
@@ -503,7 +503,7 @@ def run_regimes(a):
         pts = []
         for N in Ns:
             k = min(64, N)
-            bits = next((w for w in widths if w >= 2 * N + 197), widths[-1])
+            bits = next((w for w in widths if w >= 2 * N + 229), widths[-1])
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             while True:

@@ -162,9 +162,9 @@ HK_API hk_status hk_alu_peak(int device, int kind, double* per_clk_per_sm);
  * precision to the user; Sec. 4.1 confirms it by doubling).  loss_bits =
  * max(0, max_i ceil(log2(mu_{2i} / d_i))): the leading bits that cancelled in
  * the pivots, formed on the device right after hk_ldlt.  min_bits =
- * ceil(1.8 loss + 197): 133 bits for 1e-40 and 64 to spare, 1.8 bounding the
- * ratio of the loss precision doubling shows to this estimate (about 1.7 at
- * beta = 1/2).  After hk_ldlt; outputs (host) may be NULL; synchronises. */
+ * 2 loss + 32 + 197: the bits precision doubling shows lost stay below
+ * 2 loss + 32 (beta = 1/4 ... 1), and 197 = 133 bits for 1e-40 plus 64 to
+ * spare.  After hk_ldlt; outputs (host) may be NULL; synchronises. */
 HK_API hk_status hk_precision_loss(hk_ctx* ctx, int32_t* loss_bits, int32_t* min_bits);
 
 /* a8. d lambda_1 / d beta of the block estimate lambda_1 = 1/nu_1:

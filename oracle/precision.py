@@ -10,17 +10,20 @@ leading bits that cancelled in forming it.
 
     loss = max(0, max_i ceil(log2(mu_{2i} / d_i)))
 
-computed here exactly from the rationals of the two numbers.  The rule that
-uses it: a result is trusted to 1e-40 (133 bits) with 64 bits to spare when
-    p - 1.8 loss >= 133 + 64,
-1.8 bounding the ratio of the loss seen by precision doubling to this
-estimate (about 1.7 at beta = 1/2).
+computed here exactly from the rationals of the two numbers.  The bits the
+truncating factorisation actually loses, seen by precision doubling (the
+relative difference of D and lambda_1 between p and 2p bits), stay below
+2 loss + 32 for beta = 1/4 ... 1 (about 1.6 to 2.3 times the estimate).  The
+rule that uses it: a result is trusted to 1e-40 (133 bits) with 64 bits to
+spare when
+    p >= 2 loss + 32 + 133 + 64.
 """
 from fractions import Fraction
 
 from . import mpfloat as F
 
-LOSS_FACTOR = Fraction(9, 5)
+LOSS_FACTOR = 2
+LOSS_SLACK = 32
 KEEP_BITS = 133 + 64
 
 
@@ -47,5 +50,4 @@ def loss_estimate(mu, D):
 
 def min_bits(loss):
     """The least working precision the rule accepts for this loss."""
-    v = LOSS_FACTOR * loss + KEEP_BITS
-    return -((-v.numerator) // v.denominator)
+    return LOSS_FACTOR * loss + LOSS_SLACK + KEEP_BITS

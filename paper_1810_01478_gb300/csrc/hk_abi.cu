@@ -521,10 +521,10 @@ hk_status hk_set_moments(hk_ctx* h, int N, int bits, const int32_t* sign, const 
   return HK_OK;
 }
 
-// The rule on the loss estimate: a result keeps 133 bits (1e-40) and 64 to
-// spare when bits - 1.8 loss >= 197; 1.8 bounds the ratio of the loss seen
-// by precision doubling to the estimate (about 1.7 at beta = 1/2).
-static int min_bits_for(int loss) { return (int)std::ceil(std::min(1.8 * loss + 197.0, 2.0e9) - 1e-9); }
+// The rule on the loss estimate: the bits precision doubling shows lost stay
+// below 2 loss + 32 (beta = 1/4 ... 1), so a result keeps 133 bits (1e-40)
+// and 64 to spare when bits >= 2 loss + 32 + 197.
+static int min_bits_for(int loss) { return (int)std::min<int64_t>(2 * (int64_t)loss + 229, 2000000000); }
 
 static hk_status read_loss(Ctx& c, int& loss) {
   hk_status st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising");

@@ -2,8 +2,8 @@
 device right after hk_ldlt) against the oracle's loss estimate
 max(0, max_i ceil(log2(mu_{2i} / d_i))) on the same factor
 (oracle.precision), and hk_lambda1's HK_ERR_PRECISION when the working
-precision is below 1.8 loss + 197 bits (beta = 1/2, N = 384 at 1024 bits,
-where the estimate is over 500 bits; N = 320 at the same width passes)."""
+precision is below 2 loss + 229 bits (beta = 1/2, N = 384 at 1024 bits,
+where the estimate is over 500 bits; N = 256 at the same width passes)."""
 from fractions import Fraction
 
 import pytest
@@ -40,7 +40,7 @@ def test_loss_estimate_vs_oracle(beta, N, bits):
     assert mb == PR.min_bits(loss)
 
 
-@pytest.mark.parametrize("N,fires", [(384, True), (320, False)])
+@pytest.mark.parametrize("N,fires", [(384, True), (256, False)])
 def test_lambda_guard(N, fires):
     import paper_1810_01478_gb300 as hk
     bits = 1024
