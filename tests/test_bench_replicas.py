@@ -1,8 +1,9 @@
-"""The multi-GPU path of bench.py is replicas only: every rank solves its own
-instance, the job time is the slowest rank's, and the value counts the
-solves of all ranks.  Checked here with two gloo ranks on the CPU (no GPU):
-the cross-rank maximum, the throughput formula, and that only rank 0 of the
-reference arm prints."""
+"""Host logic of bench.py, on the CPU.  The multi-GPU path is replicas only:
+every rank solves its own instance, the job time is the slowest rank's, and
+the value counts the solves of all ranks.  Checked here with two gloo ranks
+(no GPU): the cross-rank maximum, the throughput formula, and that only rank
+0 of the reference arm prints.  Also the arithmetic of the roofline object
+and of the regimes workload's slopes."""
 import json
 import os
 import socket
