@@ -411,17 +411,27 @@ def _torch_function():
         libhk at `bits` bits and also forms d lambda_1 / d beta (the adjoint
         of hk_lambda1_grad, first-order perturbation of the block's top
         eigenvalue); backward multiplies it by the incoming gradient.  beta
-        must be 1/m (moments exact on the device); the multiprecision values
-        stay available through Hankel."""
+        = 1/m needs nothing else (moments exact on the device); beta = a/b
+        with a > 1 needs `constants` = {"gamma": (exp, limbs) of Gamma(r/a),
+        "psi": (sign, exp, limbs) of psi(r/a)}, r = 1..a-1 (the inputs of
+        hk_moments_gamma and hk_set_psi_constants).  The multiprecision
+        values stay available through Hankel."""
 
         @staticmethod
-        def forward(ctx, beta, N, k, bits, device=0):
+        def forward(ctx, beta, N, k, bits, device=0, constants=None):
             b = _exact_beta(beta.item() if hasattr(beta, "item") else beta)
+            if b.numerator > 1 and (not constants or "gamma" not in constants or "psi" not in constants):
+                raise ValueError("beta = a/b with a > 1 needs constants={'gamma': ..., 'psi': ...}")
             with Hankel(device) as h:
-                h.moments(b.numerator, b.denominator, N, bits)
+                if b.numerator == 1:
+                    h.moments(b.numerator, b.denominator, N, bits)
+                else:
+                    h.moments_gamma(b.numerator, b.denominator, N, bits, *constants["gamma"])
                 h.ldlt()
                 h.inv_block(k)
                 lam = h.lambda1(1)
+                if b.numerator > 1:
+                    h.set_psi_constants(*constants["psi"])
                 g = h.lambda1_grad()
             ctx.save_for_backward(torch.tensor(float(g[3][0]), dtype=torch.float64))
             return torch.tensor(float(lam[3][0]), dtype=torch.float64)
@@ -429,12 +439,12 @@ def _torch_function():
         @staticmethod
         def backward(ctx, grad_out):
             (g,) = ctx.saved_tensors
-            return grad_out * g.to(grad_out.device), None, None, None, None
+            return grad_out * g.to(grad_out.device), None, None, None, None, None
 
     _LAMBDA1_FN = Lambda1
     return Lambda1
 
 
-def lambda1(beta, N, k, bits, device=0):
+def lambda1(beta, N, k, bits, device=0, constants=None):
     """Differentiable lambda_1(beta) (torch.autograd); see Lambda1 above."""
-    return _torch_function().apply(beta, N, k, bits, device)
+    return _torch_function().apply(beta, N, k, bits, device, constants)

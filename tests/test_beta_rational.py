@@ -24,3 +24,12 @@ def test_exact_beta_refuses_irrational_and_large_denominators():
     for v in (1.0 / math.pi, math.sqrt(2.0) / 3.0, 1.0 / 1009.0):
         with pytest.raises(ValueError):
             _exact_beta(v)
+
+
+def test_front_end_asks_for_constants_at_rational_beta():
+    """beta = 9/20 without the Gamma and psi constants is refused before any
+    device work."""
+    import paper_1810_01478_gb300 as hk
+    for c in (None, {"gamma": ([], [])}):
+        with pytest.raises(ValueError):
+            hk.lambda1(torch.tensor(0.45, dtype=torch.float64, requires_grad=True), 48, 8, 4096, constants=c)
