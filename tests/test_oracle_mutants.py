@@ -10,8 +10,9 @@ Algorithm 4 without the negated column or without its last term, the block
 without 1/D, the smallest eigenvalue instead of the largest, a sign error in
 Gauss's digamma theorem, a gradient with the wrong sign of psi, a floor
 where the loss estimate takes a ceiling, a harmonic number one index too
-far, a missing 1/a in the Gamma-constant route to the moments, and the loss
-estimate against mu_i instead of mu_2i."""
+far, a missing 1/a in the Gamma-constant route to the moments, the loss
+estimate against mu_i instead of mu_2i, truncation errors of the wrong sign,
+and an entry sample that takes the wrong row."""
 from fractions import Fraction
 from math import factorial
 
@@ -205,3 +206,25 @@ def test_loss_estimate_wrong_moment(monkeypatch):
         return best
     monkeypatch.setattr(PR, "loss_estimate", loss_wrong)
     assert caught(TP.test_loss_estimate_closed_form_beta1)
+
+
+def test_truncation_error_sign(monkeypatch):
+    orig = EG.lambdas
+
+    def flipped(S, n_eig=3, prec=None):
+        lam, err, ev, vec = orig(S, n_eig, prec)
+        return lam, [None if e is None else -e for e in err], ev, vec   # lambda(k-1) - lambda(k)
+    monkeypatch.setattr(EG, "lambdas", flipped)
+    assert caught(TP.test_interlacing_and_precision_doubling)
+
+
+def test_subset_sampling_forgets_the_row(monkeypatch):
+    orig = LD.sample_entry
+
+    def sample_wrong(mu, r, c, n):
+        if r == c:
+            return orig(mu, r, c, n)
+        D, L = LD.ldlt_subset(mu, list(range(c + 2)), n)              # row c + 1 for row r
+        return L[c + 1][c]
+    monkeypatch.setattr(LD, "sample_entry", sample_wrong)
+    assert caught(TP.test_subset_sampling_reproduces_full_factor)
