@@ -209,18 +209,27 @@ HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
  * operand scanning), HK_PRODUCT_NTT (number-theoretic transforms of length
  * 2^a or 3 2^a modulo three primes k 3 2^11 + 1 below 2^30 and Chinese
  * remaindering; the transforms of a step's pivot column are computed once and
- * reused by every update, n <= 1024 limbs), or
- * HK_PRODUCT_AUTO (the NTT from HK_NTT_AUTO_MIN_M * 1024 bits up).  Both give
- * the same exact product, so results are identical bit for bit; this only
- * changes speed.  The paper's GMP multiplies likewise switch algorithm by size. */
+ * reused by every update, n <= 1024 limbs), HK_PRODUCT_TENSOR (from
+ * HK_TC_MIN_M * 1024 bits: the trailing update's products as bf16 GEMMs on
+ * the tensor cores, balanced 7-bit digits whose convolution sums stay below
+ * 2^24 and so are exact in fp32; the other products of the path use the
+ * NTT), or HK_PRODUCT_AUTO (the NTT from HK_NTT_AUTO_MIN_M * 1024 bits up,
+ * the tensor cores from HK_TC_AUTO_MIN_M * 1024 bits up).  All give the same
+ * exact product, so results are identical bit for bit; this only changes
+ * speed.  The paper's GMP multiplies likewise switch algorithm by size. */
 #define HK_PRODUCT_AUTO 0
 #define HK_PRODUCT_SCHOOLBOOK 1
 #define HK_PRODUCT_NTT 2
+#define HK_PRODUCT_TENSOR 3
 #define HK_NTT_AUTO_MIN_M 8
+#define HK_TC_MIN_M 8
+#define HK_TC_AUTO_MIN_M 1000
 HK_API hk_status hk_set_product_algorithm(int algorithm);
 
 /* Elementwise primitives on caller-owned DEVICE arrays of `count` numbers of
- * width `bits`, ordered on cuda_stream (no synchronisation):
+ * width `bits`, ordered on cuda_stream (no synchronisation, except that
+ * hk_div_batch and hk_fused_batch with HK_PRODUCT_TENSOR read their device
+ * flags back and synchronise):
  *   hk_fused_batch: out[i] = trunc(a[i] - x[i]*y[i])  (the update of Alg. 1/4)
  *   hk_div_batch:   out[i] = trunc(a[i] / d[i])      (d[i] != 0)
  * `out` may not alias the inputs. */
@@ -276,10 +285,15 @@ HK_API hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_
  *   limit: N * (bits/32 + 2) + bits/32 + 35 <= HK_NOALLOC_SCRATCH_WORDS,
  *          else HK_ERR_ARG (e.g. N <= 1024 at bits <= 24576)
  * The first call on a device looks the array's address up (once per device,
- * with that device current); make that first call before any stream capture.
- * Every call shares the array, so calls that overlap on the GPU race: the
- * caller serialises them.  Synchronises cuda_stream before returning and
- * reports a non-positive pivot as HK_ERR_NOT_PD. */
+ * with that device current) and keeps it for the life of the library, which
+ * therefore must not outlive a cudaDeviceReset of that device; make that
+ * first call before any stream capture begins.  Every call shares the array,
+ * so calls that overlap on the GPU race: the caller serialises them.  Each
+ * call reads the device error word back and synchronises cuda_stream before
+ * it returns, and reports device flags with the same status codes as
+ * hk_ldlt's next synchronising call (HK_ERR_NOT_PD for a non-positive pivot).
+ * Products are schoolbook (n^2 limb products) at every width, so at the NTT
+ * widths (from HK_NTT_AUTO_MIN_M * 1024 bits) it is slower than hk_ldlt. */
 #define HK_NOALLOC_SCRATCH_WORDS (1u << 20)
 HK_API hk_status hk_ldlt_noalloc(int bits, int N, const int32_t* mu_sign, const int32_t* mu_exp,
                                  const uint32_t* mu_limbs, int32_t* f_sign, int32_t* f_exp, uint32_t* f_limbs,

@@ -29,8 +29,9 @@ EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_
            "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
            "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run",
            "hk_set_product_algorithm", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"]
-HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT = 0, 1, 2
+HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT, HK_PRODUCT_TENSOR = 0, 1, 2, 3
 HK_NTT_AUTO_MIN_M = 8  # include/hk.h: AUTO uses NTT products from 32 * 8 limbs (8192 bits)
+HK_TC_MIN_M = 8        # include/hk.h: tensor-core products exist from 8192 bits
 
 
 class Instance(ctypes.Structure):
@@ -239,7 +240,7 @@ def hk_div_batch(bits, count, a, d, out, stream=None):
 
 
 def hk_set_product_algorithm(algorithm):
-    """HK_PRODUCT_AUTO / HK_PRODUCT_SCHOOLBOOK / HK_PRODUCT_NTT (process-wide)."""
+    """HK_PRODUCT_AUTO / _SCHOOLBOOK / _NTT / _TENSOR (process-wide)."""
     _check(load().hk_set_product_algorithm(algorithm), what="hk_set_product_algorithm")
 
 

@@ -11,6 +11,8 @@ enum ErrBits : int {
   ERR_LOOP = 2,          // a correction loop exceeded its bound (should never happen)
   ERR_PRECISION = 4,     // the working precision was too low for the requested result
   ERR_ARG = 8,
+  ERR_TIMEOUT = 16,      // a bounded device wait gave up (the kernel returned without finishing);
+                         // bits 8..11 then name the wait (a kernel's own numbering of its call sites)
 };
 
 

@@ -60,6 +60,14 @@ struct Ctx {
   bool cols_marked = false;
   uint32_t* ntt_buf2 = nullptr;
   size_t ntt_cap2 = 0;  // words
+  // tensor-core products of the trailing update (tc.cuh): digit matrix of the
+  // step's B column (kgroup-major, N + 128 rows), digits of its U column, and
+  // the product buffers of the persistent kernel's blocks
+  uint16_t* tc_db = nullptr;
+  uint16_t* tc_du = nullptr;
+  uint32_t* tc_p = nullptr;
+  size_t tc_db_cap = 0, tc_du_cap = 0, tc_p_cap = 0;  // elements
+  double tc_mmas = 0.0;  // tcgen05.mma instructions of the profiled trailing launches
   // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
   std::map<std::string, DevVec> pool;
   const uint32_t* one_mant = nullptr;  // pool "one" holds 1 while its mant is this (cleared on reallocation)
@@ -86,6 +94,9 @@ struct Ctx {
 hk_status set_error(Ctx& c, hk_status s, const std::string& msg);
 hk_status check_cuda(Ctx& c, cudaError_t e, const char* what);
 hk_status read_device_flags(Ctx& c);  // synchronises
+// The status (and a message) that a device flags word (ErrBits) maps to;
+// every entry point that reads the flags reports them through this.
+hk_status status_of_flags(int flags, const char** msg);
 
 // Per-width operations, one instantiation per limb count M (= n/32).
 struct OpsTable {
@@ -94,7 +105,8 @@ struct OpsTable {
   hk_status (*inv_block)(Ctx&);
   hk_status (*lambda)(Ctx&, int n_eig);
   hk_status (*grad)(Ctx&, int32_t* sgn, int32_t* exp, uint32_t* mant, double* f64);
-  cudaError_t (*fused_batch)(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count, cudaStream_t s);
+  // flags: host, the device flags (ErrBits) of paths that read them back, else 0
+  cudaError_t (*fused_batch)(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count, cudaStream_t s, int* flags);
   cudaError_t (*div_batch)(MPVec a, MPVec d, MPVec out, int64_t count, int* err, cudaStream_t s);
   // Algorithm 1 on caller-provided buffers (no allocation): see hk_ldlt_noalloc
   cudaError_t (*ldlt_raw)(MPVec mu, MPVec A, MPVec U, uint32_t* rec, int* rec_meta, int* err, int N,
@@ -111,6 +123,8 @@ inline void count_launch(Ctx& c, int64_t k = 1) { c.launches += k; }
 // Product algorithm of the wide kernels (hk_set_product_algorithm).
 int product_algorithm();
 bool use_ntt(int M);
+// Tensor-core products (tcgen05) for the trailing update at this width.
+bool use_tc(int M);
 // NTT constants for n limbs on the current device (tables built on first use).
 NttConst ntt_const(int n);
 

@@ -42,6 +42,12 @@ bool use_ntt(int M) {
   return M >= HK_NTT_AUTO_MIN_M && 32 * M * 2 <= NTT_LMAX;
 }
 
+bool use_tc(int M) {
+  const int a = product_algorithm();
+  if (M < HK_TC_MIN_M || !use_ntt(M)) return false;
+  return a == HK_PRODUCT_TENSOR || (a == HK_PRODUCT_AUTO && M >= HK_TC_AUTO_MIN_M);
+}
+
 namespace {
 // the three largest primes k 3 2^11 + 1 below 2^30 (p1 > p2 > p3, p1 < 2 p3)
 // with primitive roots 23, 5, 10
@@ -199,18 +205,42 @@ size_t prof_mark(Ctx& c) {
   return c.ev_used++;
 }
 
+hk_status status_of_flags(int flags, const char** msg) {
+  const char* m = "";
+  hk_status st = HK_OK;
+  // a kernel that gave up a wait left its results unfinished, so whatever
+  // later kernels flagged may follow from that: report it first
+  if (flags & ERR_TIMEOUT) {
+    st = HK_ERR_TIMEOUT;
+    m = "a bounded device wait gave up";
+  } else if (flags & ERR_NOT_PD) {
+    st = HK_ERR_NOT_PD;
+    m = "a pivot d_i <= 0: raise the working precision";
+  } else if (flags & ERR_PRECISION) {
+    st = HK_ERR_PRECISION;
+    m = "working precision too low";
+  } else if (flags & ERR_LOOP) {
+    st = HK_ERR_CUDA;
+    m = "internal correction loop exceeded its bound";
+  } else if (flags & ERR_ARG) {
+    st = HK_ERR_ARG;
+    m = "invalid device operand (zero divisor or capacity)";
+  }
+  if (msg) *msg = m;
+  return st;
+}
+
 hk_status read_device_flags(Ctx& c) {
   hk_status st = check_cuda(c, cudaStreamSynchronize(c.stream), "synchronising");
   if (st != HK_OK) return st;
   int flags = 0;
   st = check_cuda(c, cudaMemcpy(&flags, c.d_err, sizeof(int), cudaMemcpyDeviceToHost), "reading device flags");
   if (st != HK_OK) return st;
-  if (flags & ERR_NOT_PD)
-    return set_error(c, HK_ERR_NOT_PD, "a pivot d_i <= 0: raise the working precision");
-  if (flags & ERR_PRECISION) return set_error(c, HK_ERR_PRECISION, "working precision too low");
-  if (flags & ERR_LOOP) return set_error(c, HK_ERR_CUDA, "internal correction loop exceeded its bound");
-  if (flags & ERR_ARG) return set_error(c, HK_ERR_ARG, "invalid device operand (zero divisor or capacity)");
-  return HK_OK;
+  const char* msg = nullptr;
+  st = status_of_flags(flags, &msg);
+  if (st == HK_ERR_TIMEOUT && (flags >> 8)) return set_error(c, st, std::string(msg) + " (wait site " +
+                                                                        std::to_string((flags >> 8) & 15) + ")");
+  return st == HK_OK ? HK_OK : set_error(c, st, msg);
 }
 
 }  // namespace hk
@@ -342,6 +372,9 @@ void hk_destroy(hk_ctx* h) {
   if (c.rec) cudaFree(c.rec);
   if (c.ntt_buf) cudaFree(c.ntt_buf);
   if (c.ntt_buf2) cudaFree(c.ntt_buf2);
+  if (c.tc_db) cudaFree(c.tc_db);
+  if (c.tc_du) cudaFree(c.tc_du);
+  if (c.tc_p) cudaFree(c.tc_p);
   if (c.d_err) cudaFree(c.d_err);
   delete h;
 }
@@ -704,7 +737,7 @@ hk_status hk_export(hk_ctx* h, int what, int64_t first, int64_t count, int32_t* 
 }
 
 hk_status hk_set_product_algorithm(int algorithm) {
-  if (algorithm < HK_PRODUCT_AUTO || algorithm > HK_PRODUCT_NTT) return HK_ERR_ARG;
+  if (algorithm < HK_PRODUCT_AUTO || algorithm > HK_PRODUCT_TENSOR) return HK_ERR_ARG;
   g_product_alg.store(algorithm);
   return HK_OK;
 }
@@ -822,10 +855,12 @@ hk_status hk_fused_batch(int bits, int64_t count, const int32_t* a_sign, const i
   if (!a_sign || !a_exp || !a_limbs || !x_sign || !x_exp || !x_limbs || !y_sign || !y_exp || !y_limbs ||
       !out_sign || !out_exp || !out_limbs)
     return HK_ERR_ARG;
+  int flags = 0;
   const cudaError_t e = ops_for(bits / 1024)->fused_batch(
       cvec(a_sign, a_exp, a_limbs), cvec(x_sign, x_exp, x_limbs), cvec(y_sign, y_exp, y_limbs),
-      MPVec{out_sign, out_exp, out_limbs}, count, static_cast<cudaStream_t>(cuda_stream));
-  return e == cudaSuccess ? HK_OK : HK_ERR_CUDA;
+      MPVec{out_sign, out_exp, out_limbs}, count, static_cast<cudaStream_t>(cuda_stream), &flags);
+  if (e != cudaSuccess) return HK_ERR_CUDA;
+  return status_of_flags(flags, nullptr);
 }
 
 hk_status hk_div_batch(int bits, int64_t count, const int32_t* a_sign, const int32_t* a_exp,

@@ -26,7 +26,10 @@ constexpr size_t kScratchWords = HK_NOALLOC_SCRATCH_WORDS;
 static __device__ __align__(256) uint32_t hk_noalloc_scratch[kScratchWords];
 
 // Host code cannot use the array's name as a device address; the address is
-// looked up once per device (with that device current) and cached here.
+// looked up once per device (with that device current) and cached here.  The
+// cache lives as long as the library: a cudaDeviceReset (or anything else
+// that unloads the device's module) while the library stays loaded would
+// leave a stale address here, so the library does not support that.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 uint32_t* g_scratch[kMaxDevices] = {};
@@ -81,7 +84,6 @@ extern "C" hk_status hk_ldlt_noalloc(int bits, int N, const int32_t* mu_sign, co
   if (cudaMemcpyAsync(&flags, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return HK_ERR_CUDA;
-  if (flags & ERR_NOT_PD) return HK_ERR_NOT_PD;
-  if (flags) return HK_ERR_CUDA;
-  return HK_OK;
+  // the same status for the same device flags as every other entry point
+  return status_of_flags(flags, nullptr);
 }

@@ -6,6 +6,7 @@
 
 #include "ctx.h"
 #include "k_ldlt.cuh"
+#include "tc.cuh"
 
 namespace hk {
 
@@ -53,10 +54,90 @@ struct Ops {
     return std::max(1, per_sm) * sm_count(device);
   }
 
-  static cudaError_t fused_batch(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count, cudaStream_t s) {
+  // ------------------------------------------------------------------ tensor cores
+  static constexpr bool kTc = M >= HK_TC_MIN_M;
+  static constexpr size_t tc_smem = TcSmem<M>::bytes;
+
+  // items of step i (TcTrail::items on the host)
+  static int tc_trail_items(int N, int i) {
+    const int m = N - 1 - i;
+    int s = 0;
+    for (int kt = 0; m - 1 > 128 * kt; ++kt) s += m - 128 * kt;
+    return s;
+  }
+  // tcgen05.mma instructions of one 128-row item (the same walk as the MMA warp)
+  static double tc_mmas_per_item() {
+    using S = TcShape<M>;
+    double c = 0;
+    for (int t = 0; t < S::T; ++t) {
+      const int lo = std::max(0, 256 * t - S::D + 1) >> 6, hi = std::min(S::D - 1, 256 * t + 255) >> 6;
+      for (int kb = lo; kb <= hi; ++kb)
+        for (int s4 = 0; s4 < 4; ++s4) {
+          const int k0 = 64 * kb + 16 * s4;
+          if (!(k0 > 256 * t + 255 || k0 + 15 < 256 * t - S::D + 1)) c += 1;
+        }
+    }
+    return c;
+  }
+  static int tc_grid(int device) { return std::max(1, sm_count(device) - 1); }
+  static size_t tc_p_words(int grid) { return (size_t)grid * 2 * TC_ROWS * TcShape<M>::PL; }
+
+  template <class Items>
+  static cudaError_t tc_launch(const Items& it, int n_items, const uint16_t* DB, int pitch, const uint16_t* DU,
+                               uint32_t* P, int grid, int* err, cudaStream_t s) {
+    if constexpr (kTc) {
+      cudaError_t e = cudaFuncSetAttribute(k_tc_fused<M, Items>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)tc_smem);
+      if (e != cudaSuccess) return e;
+      const int g = std::min(grid, n_items);
+      if (g <= 0) return cudaSuccess;
+      k_tc_fused<M, Items><<<g, TC_THREADS, tc_smem, s>>>(it, DB, pitch, DU, P, err);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorNotSupported;
+    }
+  }
+
+  // digits of count numbers mant[(first + t) n] into rows row0 + t of DU (layout 0) or DB (layout 1)
+  static void tc_digits(const uint32_t* mant, int64_t first, int count, int row0, uint16_t* out, int layout,
+                        int pitch, int device, cudaStream_t s) {
+    if constexpr (kTc) {
+      if (count <= 0) return;
+      const int g = (int)std::min<int64_t>((count + WARPS - 1) / WARPS, 4 * sm_count(device));
+      k_tc_digits<M><<<g, 32 * WARPS, 0, s>>>(mant, first, count, row0, out, layout, pitch);
+    }
+  }
+
+  static cudaError_t fused_batch(MPVec a, MPVec x, MPVec y, MPVec out, int64_t count, cudaStream_t s, int* flags) {
+    if (flags) *flags = 0;
     if (count <= 0) return cudaSuccess;
     int dev = 0;
     cudaGetDevice(&dev);
+    if (kTc && use_tc(M) && count < (1 << 30)) {
+      // x[e] is the U column of item e, y[e] its single digit row; every launch
+      // is checked for device flags (a stray limb or a wait that gave up)
+      using S = TcShape<M>;
+      const int cnt = (int)count, pitch = cnt + TC_ROWS, grid = tc_grid(dev);
+      const size_t db = (size_t)S::ND * pitch, du = (size_t)S::ND * cnt, pw = tc_p_words(grid);
+      uint8_t* buf = nullptr;
+      cudaError_t e = cudaMallocAsync(&buf, (db + du) * 2 + pw * 4 + 16, s);
+      if (e != cudaSuccess) return e;
+      uint16_t* DB = reinterpret_cast<uint16_t*>(buf);
+      uint16_t* DU = DB + db;
+      uint32_t* P = reinterpret_cast<uint32_t*>(DU + du);
+      int* flag = reinterpret_cast<int*>(P + pw);
+      cudaMemsetAsync(DB, 0, db * 2, s);
+      cudaMemsetAsync(flag, 0, sizeof(int), s);
+      tc_digits(x.mant, 0, cnt, 0, DU, 0, 0, dev, s);
+      tc_digits(y.mant, 0, cnt, 0, DB, 1, pitch, dev, s);
+      e = tc_launch(TcBatch<M>{a, x, y, out, cnt}, cnt, DB, pitch, DU, P, grid, flag, s);
+      int host_flag = 0;
+      if (e == cudaSuccess) e = cudaMemcpyAsync(&host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      cudaFreeAsync(buf, s);
+      if (flags) *flags = host_flag;
+      return e;
+    }
     if (use_ntt(M)) {
       const NttConst nc = ntt_const(n);
       const size_t per = (size_t)NTT_Q * nc.L;
@@ -196,6 +277,32 @@ struct Ops {
       if ((st = check_cuda(c, allow_smem(k_scale_ntt<M>, ntt_smem), "smem attribute")) != HK_OK) return st;
       scale_ntt_res = resident_blocks(k_scale_ntt<M>, 32 * NTW, ntt_smem, c.device);
     }
+    // tensor-core products: digit matrices and the blocks' product buffers
+    const bool tc = ntt && kTc && use_tc(M);
+    const int tc_g = tc_grid(c.device);
+    const int tc_pitch = N + TC_ROWS;
+    if (tc) {
+      using S = TcShape<M>;
+      auto grow = [&](auto*& p, size_t& cap, size_t need, size_t elem) -> hk_status {
+        if (cap >= need) return HK_OK;
+        if (p) {
+          cudaStreamSynchronize(c.stream);
+          cudaFree(p);
+          p = nullptr;
+          cap = 0;
+        }
+        hk_status r = check_cuda(c, cudaMalloc((void**)&p, need * elem), "allocating the tensor-core buffers");
+        if (r == HK_OK) cap = need;
+        return r;
+      };
+      if ((st = grow(c.tc_db, c.tc_db_cap, (size_t)S::ND * tc_pitch, 2)) ||
+          (st = grow(c.tc_du, c.tc_du_cap, (size_t)S::ND * N, 2)) ||
+          (st = grow(c.tc_p, c.tc_p_cap, tc_p_words(tc_g), 4)))
+        return st;
+      // rows past N stay zero: they fill the last 128-row tile of a column
+      if ((st = check_cuda(c, cudaMemsetAsync(c.tc_db, 0, (size_t)S::ND * tc_pitch * 2, c.stream), "clearing")))
+        return st;
+    }
     uint32_t* FU = c.ntt_buf;
     uint32_t* FB = c.ntt_buf ? c.ntt_buf + per * (size_t)N : nullptr;
     uint32_t* FRD = c.ntt_buf ? c.ntt_buf + 2 * per * (size_t)N : nullptr;
@@ -260,8 +367,17 @@ struct Ops {
         const int gq = (int)std::min<int64_t>((rows + NTW - 1) / NTW, scale_ntt_res);
         k_scale_ntt<M><<<gq, 32 * NTW, ntt_smem, s>>>(c.A.view(), c.U.view(), N, i, FU, FRD, FB, c.rec_meta, nc,
                                                        c.d_err);
-        k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FB, nc, 1);
+        // with tensor-core products only the look-ahead entry (i+1, i+1) needs F(B_i)
+        const bool tc_step = tc && rows >= HK_TC_MIN_ROWS;
+        const int fb_rows = tc_step ? 1 : (int)rows;
+        k_ntt_fwd<M><<<std::min(g, fb_rows), 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), fb_rows,
+                                                                         FB, nc, 1);
         count_launch(c, 2);
+        if (tc_step) {
+          tc_digits(c.U.mant, i + 1, (int)rows, i + 1, c.tc_du, 0, 0, c.device, s);
+          tc_digits(c.A.mant, tri_pos(N, i + 1, i), (int)rows, i + 1, c.tc_db, 1, tc_pitch, c.device, s);
+          count_launch(c, 2);
+        }
         if (i < (int)c.ev_col.size()) cudaEventRecord(c.ev_col[i], s);  // column i of L is final
       } else {
         k_scale<M><<<gs, 32 * WARPS, div_smem, s>>>(c.A.view(), c.U.view(), N, i, c.rec, c.rec_meta, c.d_err);
@@ -281,7 +397,16 @@ struct Ops {
       // ... while the main stream updates the rest of the trailing triangle
       if (T > 1) {
         const size_t e1 = c.prof ? prof_mark(c) : 0;
-        trailing(i, 1, T);
+        const bool tc_step = tc && rows >= HK_TC_MIN_ROWS;
+        if (tc_step) {
+          const int items = tc_trail_items(N, i);
+          const cudaError_t e = tc_launch(TcTrail<M>{c.A.view(), c.U.view(), N, i}, items, c.tc_db, tc_pitch,
+                                          c.tc_du, c.tc_p, tc_g, c.d_err, s);
+          if ((st = check_cuda(c, e, "launching the tensor-core update")) != HK_OK) return st;
+          if (c.prof) c.tc_mmas += items * tc_mmas_per_item();
+        } else {
+          trailing(i, 1, T);
+        }
         if (c.prof) {
           c.trail_ev.push_back({e1, prof_mark(c)});
           c.trail_macs += (double)(T - 1) * n * n;  // n^2 limb products per fused operation

@@ -13,6 +13,8 @@ asked) and stores, in tests/golden/<name>.json:
   x_sha256                the same for X (row major N x k)
 Usage:  python tests/golden/make_golden.py <target> [<target> ...]
 Targets: c1, c2, c5_512_4096, c5_768_4096, c5_1024_4096, c5_1024_8192,
+         w_256_24576, w_160_16384, w_320_24576 (whole factors at 24576 and
+         16384 bits),
          c3const (Gamma(r/a) constants for beta = 9/20, 11/20),
          c3_<a>_<b>_<N> (one batched-config instance; beta = a/b, k = 16,
          bits = 32 N, non-dyadic moments from the stored constants)
@@ -37,8 +39,13 @@ TARGETS = {
     "c2": dict(beta=(1, 2), N=256, k=16, bits=8192, grad=True, fd=True),
     "c5_512_4096": dict(beta=(1, 2), N=512, k=32, bits=4096, grad=False, fd=False),
     "c5_768_4096": dict(beta=(1, 2), N=768, k=32, bits=4096, grad=False, fd=False),
-    "c5_1024_4096": dict(beta=(1, 2), N=1024, k=32, bits=4096, grad=False, fd=False),
+    "c5_1024_4096": dict(beta=(1, 2), N=1024, k=32, bits=4096, grad=True, fd=False),
     "c5_1024_8192": dict(beta=(1, 2), N=1024, k=32, bits=8192, grad=False, fd=False),
+    # whole factors at the widest product widths the library runs (M = 24, 16)
+    "w_256_24576": dict(beta=(1, 2), N=256, k=32, bits=24576, grad=True, fd=False),
+    "w_160_16384": dict(beta=(1, 2), N=160, k=32, bits=16384, grad=True, fd=False),
+    # N > 256: the first steps of Algorithm 1 have at least 256 trailing rows
+    "w_320_24576": dict(beta=(1, 2), N=320, k=32, bits=24576, grad=False, fd=False),
 }
 
 

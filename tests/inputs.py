@@ -11,6 +11,9 @@ Recipes
   overlap closely (the common case of the factorisation, including near-total
   cancellation where a is the product's leading limbs), or sit far apart
   (gaps of up to 4n limbs either way), or one operand is zero.
+* ``digit_extreme_mant``: the mantissa whose 7-bit groups are 64, 63, 63, ...
+  (top limb made non-zero): its balanced 7-bit digits are all -64, the
+  largest digit magnitudes a tensor-core product meets.
 * ``measure_moments``: mu_j = sum_m w_m t_m^j for a random discrete positive
   measure (integer weights w_m, distinct integer nodes t_m >= 1): the Hankel
   matrix of such moments is exactly positive definite while N <= #atoms.
@@ -37,6 +40,12 @@ def rand_mant(rng, n, kind="uniform"):
         m = rng.getrandbits(32 * n)
         return m | (((1 << (32 * t)) - 1) << (32 * (n - t)))
     raise ValueError(kind)
+
+
+def digit_extreme_mant(n):
+    m = 64 | sum(63 << (7 * k) for k in range(1, (32 * n) // 7 + 1))
+    m &= (1 << (32 * n)) - 1
+    return m | (1 << (32 * n - 1))
 
 
 def rand_num(rng, n, e_lo=-8, e_hi=8, kinds=("uniform",)):

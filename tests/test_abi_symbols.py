@@ -46,3 +46,22 @@ def test_calls_without_a_context_fail_cleanly():
     assert L.hk_inv_block(None, 4) == hk.HK_ERR_ARG
     assert L.hk_fused_batch(4096, 1, *([None] * 12), None) == hk.HK_ERR_ARG
     assert L.hk_fused_batch(1000, 1, *([None] * 12), None) == hk.HK_ERR_ARG
+
+
+def test_noalloc_argument_checks_need_no_device():
+    """hk_ldlt_noalloc rejects bad sizes and null arrays before it touches the
+    device or its scratch array: the size limit N (bits/32 + 2) + bits/32 + 35
+    <= HK_NOALLOC_SCRATCH_WORDS, a width that is not a multiple of 1024, and
+    missing arrays all give HK_ERR_ARG with no GPU present."""
+    import paper_1810_01478_gb300 as hk
+    L = hk.load()
+    nulls = [None] * 6
+    assert L.hk_ldlt_noalloc(24576, 2000, *nulls, None) == hk.HK_ERR_ARG   # beyond the scratch array
+    assert L.hk_ldlt_noalloc(24576, 1024, *nulls, None) == hk.HK_ERR_ARG   # fits, but null arrays
+    assert L.hk_ldlt_noalloc(1000, 16, *nulls, None) == hk.HK_ERR_ARG      # not a multiple of 1024
+    assert L.hk_ldlt_noalloc(4096, 0, *nulls, None) == hk.HK_ERR_ARG       # N < 1
+    # the limit itself: 2^20 words hold N = 1360 at 24576 bits (N (768 + 2) + 768 + 35 words at most),
+    # not N = 1361
+    words = 1 << 20
+    assert 1360 * 770 + 768 + 35 <= words < 1361 * 770 + 768 + 32
+    assert L.hk_ldlt_noalloc(24576, 1361, *nulls, None) == hk.HK_ERR_ARG

@@ -7,9 +7,11 @@ set {0..c} U {r} (oracle.ldlt.sample_entry, which reproduces the full
 factor's entry exactly), the first 40 rows of X (which depend only on the
 leading 40 x 40 block), lambda_1..3 against the oracle's N = 1024 runs
 (tests/golden/c5_1024_*.json, accurate far beyond 1e-40 at 4096 bits), and
-the gradient by precision doubling.  At 4096 bits (schoolbook products) and
-8192 bits (NTT products) the whole N = 1024 factor and X are compared bit for
-bit through their SHA-256 digests.
+the gradient against the oracle's analytic gradient at N = 1024 (and by
+precision doubling).  At 4096 bits (schoolbook products) and 8192 bits (NTT
+products) the whole N = 1024 factor and X are compared bit for bit through
+their SHA-256 digests; at the widest widths the whole factor and X are
+compared at N = 256 and N = 320 (24576 bits) and N = 160 (16384 bits).
 """
 import json
 import os
@@ -81,6 +83,12 @@ def test_bench_workload_sampled_parity():
                 for j in range(3):
                     want = mpm.mpf(gd["lambdas"][j])
                     assert abs(value(lam[0][j], lam[1][j], lam[2][j]) - want) / want < TOL, (name, j)
+        # the gradient against the oracle's (analytic, at 4096 bits: its error is far below 1e-40)
+        gd = golden("c5_1024_4096")
+        with mpm.workprec(2 * bits):
+            want = mpm.mpf(gd["grad"])
+            got = value(g[0][0], g[1][0], g[2][0])
+            assert abs(got - want) / abs(want) < TOL
         # the gradient at half the precision agrees (precision doubling)
         h2, lam2, g2 = run(hk, bits // 2)
         h2.close()
@@ -136,3 +144,31 @@ def test_sweep_sizes(n_):
                 for j in range(3):
                     want = mpm.mpf(gd["lambdas"][j])
                     assert abs(value(s[j], e[j], m[j]) - want) / want < TOL, (n_, bits, j)
+
+
+@pytest.mark.parametrize("name", ["w_256_24576", "w_160_16384", "w_320_24576"])
+def test_widest_widths_whole_factor(name):
+    """The whole factor and X bit for bit at 24576 bits (M = 24 limbs per
+    lane: every step shape of the widest product width, from the first
+    steps to the late ones) and at 16384 bits (M = 16), with lambda_1..3 and,
+    where the oracle computed it, the gradient to 1e-40."""
+    import paper_1810_01478_gb300 as hk
+    from tests.digest import factor_digest, x_digest
+    gd = golden(name)
+    N_, k_, bits = gd["N"], gd["k"], gd["bits"]
+    hk.load()
+    with hk.Hankel(0) as h:
+        h.moments(1, 2, N_, bits)
+        h.ldlt()
+        h.inv_block(k_)
+        assert factor_digest(h, hk, N_) == gd["factor_sha256"]
+        assert x_digest(h, hk, N_, k_) == gd["x_sha256"]
+        s, e, m, _, _ = h.lambda1(3)
+        g = h.lambda1_grad() if "grad" in gd else None
+        with mpm.workprec(2 * bits):
+            for j in range(3):
+                want = mpm.mpf(gd["lambdas"][j])
+                assert abs(value(s[j], e[j], m[j]) - want) / want < TOL, (name, j)
+            if g is not None:
+                want = mpm.mpf(gd["grad"])
+                assert abs(value(g[0][0], g[1][0], g[2][0]) - want) / abs(want) < TOL

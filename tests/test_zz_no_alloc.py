@@ -1,12 +1,14 @@
 """hk_ldlt_noalloc (the allocation-free factorisation) gives the same factor
-as hk_ldlt, bit for bit, on two calls in a row.
+as hk_ldlt, bit for bit, on calls in a row.
 
 The entry point exists for callers that cannot let a library allocate device
-memory; its scratch is one fixed array that every call reuses, so the second
+memory; its scratch is one fixed array that every call reuses, so each later
 call (a different size and width) also checks that nothing stale from the
-first one leaks into the result.  This file is collected last on purpose.
+one before leaks into the result.  The third call is at 8192 bits, where
+hk_ldlt (AUTO) takes NTT products and NTT quotients while hk_ldlt_noalloc
+keeps its schoolbook kernels: there the two share no product code.  This
+file is collected last on purpose.
 """
-import numpy as np
 import pytest
 
 from tests.layout import DevNums, from_arrays
@@ -23,12 +25,13 @@ def reference_factor(hk, N, bits):
     return mu, fac
 
 
-def test_ldlt_noalloc_matches_ldlt_on_two_calls():
+def test_ldlt_noalloc_matches_ldlt_on_calls_in_a_row():
     import torch
     import paper_1810_01478_gb300 as hk
     hk.load()
+    hk.hk_set_product_algorithm(hk.HK_PRODUCT_AUTO)
     stream = torch.cuda.current_stream().cuda_stream
-    for N, bits in [(48, 4096), (33, 2048)]:
+    for N, bits in [(48, 4096), (33, 2048), (40, 8192)]:
         n = bits // 32
         mu, want = reference_factor(hk, N, bits)
         MU = DevNums(mu, n=n)
