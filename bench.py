@@ -265,6 +265,61 @@ def trailing_roofline(prof, n, ntt, sms, sm_max, rates, traffic_per_update, issu
                 schoolbook_equiv=schoolbook)
 
 
+def measured_peaks():
+    """MEASURED_PEAKS.json (written beside this file by the GPU pool's driver), or None."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return None
+
+
+def tc_digits(n):
+    """Balanced 7-bit digits per n-limb number in the tensor-core products."""
+    return (32 * n) // 7 + 2
+
+
+def tc_updates(N, min_rows):
+    """Fused updates of the tensor-core launches of one LDL^T: every step whose
+    trailing triangle has at least min_rows rows, less its look-ahead entry."""
+    tot = 0
+    for i in range(N - 1):
+        rows = N - 1 - i
+        if rows >= min_rows:
+            tot += rows * (rows + 1) // 2 - 1
+    return tot
+
+
+def tensor_roofline(prof, N, n, min_rows, traffic_per_update, solves):
+    """The roofline object of the tensor-core trailing update: algorithmic
+    bf16 flops (2 D^2 per fused update, D balanced 7-bit digits per number:
+    the digit convolution each product is) per second of its launches'
+    device time, against the measured cuBLAS bf16 throughput sustained over a
+    long run (the launches run inside a six-second step)."""
+    launches = max(prof["tc_launches"], 1)
+    sec = prof["tc_ms"] / 1e3
+    D = tc_digits(n)
+    upd = tc_updates(N, min_rows) * solves  # the profile covers `solves` factorisations
+    alg = 2.0 * D * D * upd
+    executed = prof["tc_mmas"] * 2.0 * 128 * 256 * 16
+    pk = measured_peaks()
+    if pk and pk.get("bf16_tflops_sustained"):
+        peak, src = float(pk["bf16_tflops_sustained"]), "of measured (bf16_tflops_sustained, MEASURED_PEAKS.json)"
+    else:
+        peak, src = 1700.0, "of fallback (1.7 PFLOP/s bf16 sustained)"
+    achieved = alg / sec / 1e12
+    return dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                traffic=traffic_per_update * upd / launches if traffic_per_update is not None else None,
+                kernel="k_tc_fused (Algorithm 1 trailing update, bf16 tcgen05 digit-convolution GEMMs)",
+                peak_note=src,
+                work_per_update=f"2 D^2 = {2 * D * D} flops (D = {D} balanced 7-bit digits per number)",
+                updates=upd, launches=int(prof["tc_launches"]),
+                executed_tflops=executed / sec / 1e12, executed_frac=executed / sec / 1e12 / peak,
+                executed_note="tcgen05.mma instructions issued (128 x 256 x 16 each, including the padding of "
+                              "partial 128-row tiles and of the digit bands' edges) per second",
+                schoolbook_equiv_tlimb_macs=upd * n * n / sec / 1e12)
+
+
 def run_ours(a):
     import torch
     ws, rank, local = dist_env()
@@ -331,7 +386,24 @@ def run_ours(a):
                 issue = t.get("issue_active_frac")
         except (ValueError, KeyError):
             traffic_per_update = issue = None
-    roofline = trailing_roofline(prof, n, ntt, sms, sm_max, rates, traffic_per_update, issue)
+    ntt_roof = trailing_roofline(prof, n, ntt, sms, sm_max, rates, traffic_per_update, issue)
+    if prof.get("tc_launches", 0) > 0:
+        tc_traffic = None
+        tp2 = os.path.join(ROOT, "profiles", "tc_traffic.json")
+        if os.path.exists(tp2):
+            try:
+                t = json.load(open(tp2))
+                if t.get("bits") == a.bits and t.get("kernel_source_sha") == kernel_sha(("tc.cuh", "mp_warp.cuh")):
+                    tc_traffic = t["bytes_per_update"]
+            except (ValueError, KeyError):
+                tc_traffic = None
+        roofline = tensor_roofline(prof, a.N, n, hk.HK_TC_MIN_ROWS, tc_traffic, a.steps)
+        roofline["ntt_steps"] = dict(note="the trailing launches of the last steps (fewer than "
+                                          f"{hk.HK_TC_MIN_ROWS} rows) and the look-ahead entries keep NTT "
+                                          "products; these figures cover every trailing launch",
+                                     ms=prof["trailing_ms"] - prof["tc_ms"], measured_rates=ntt_roof.get("measured_rates"))
+    else:
+        roofline = ntt_roof
     d2h = ne * (8 + 4 * n) + min(ne, a.k - 1) * (8 + 4 * n) + (8 + 4 * n)
     lam_f64 = lam[3].tolist()
     out = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=ws, steps=a.steps, warmup=a.warmup,
@@ -347,7 +419,8 @@ def run_ours(a):
                phases_ms=dict(moments=prof["moments_ms"] / a.steps, ldlt=prof["ldlt_ms"] / a.steps,
                               trailing=prof["trailing_ms"] / a.steps, scale=prof["scale_ms"] / a.steps,
                               invblock=prof["invblock_ms"] / a.steps,
-                              eig=prof["eig_ms"] / a.steps, grad=prof["grad_ms"] / a.steps),
+                              eig=prof["eig_ms"] / a.steps, grad=prof["grad_ms"] / a.steps,
+                              trailing_tensor=prof["tc_ms"] / a.steps),
                result=dict(lambda_f64=lam_f64, trunc_err_f64=lam[4].tolist(), dlambda_dbeta_f64=gr[3].tolist()[0]),
                clocks=clk)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
@@ -359,11 +432,11 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
-def kernel_sha():
+def kernel_sha(files=("mp_warp.cuh", "ntt.cuh", "k_ldlt.cuh")):
     import hashlib
     hsh = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1810_01478_gb300", "csrc")
-    for f in ("mp_warp.cuh", "ntt.cuh", "k_ldlt.cuh"):
+    for f in files:
         hsh.update(open(os.path.join(d, f), "rb").read())
     return hsh.hexdigest()[:16]
 

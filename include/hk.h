@@ -199,8 +199,11 @@ HK_API hk_status hk_export(hk_ctx* ctx, int what, int64_t first, int64_t count, 
  *   [3] algorithmic limb products of those launches (n^2 per fused update)
  *   [4] moments ms, [5] LDL^T ms, [6] Algorithm 4 + block ms,
  *   [7] eigenvalues ms, [8] gradient ms,
- *   [9] column scale (B_i) and its transforms within the LDL^T, ms */
-#define HK_PROFILE_FIELDS 10
+ *   [9] column scale (B_i) and its transforms within the LDL^T, ms
+ *   [10] device time of the trailing-update launches with tensor-core
+ *        products (included in [1]), ms; [11] their number; [12] the
+ *        tcgen05.mma instructions they issued (M = 128, N = 256, K = 16 each) */
+#define HK_PROFILE_FIELDS 13
 HK_API hk_status hk_set_profiling(hk_ctx* ctx, int on);
 HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 
@@ -223,7 +226,11 @@ HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 #define HK_PRODUCT_TENSOR 3
 #define HK_NTT_AUTO_MIN_M 8
 #define HK_TC_MIN_M 8
-#define HK_TC_AUTO_MIN_M 1000
+#define HK_TC_AUTO_MIN_M 12
+/* With tensor-core products, steps of Algorithm 1 whose trailing triangle has
+ * fewer rows than this keep NTT products (too few 128-row work items to fill
+ * the GPU), and so does each step's look-ahead entry (i+1, i+1). */
+#define HK_TC_MIN_ROWS 256
 HK_API hk_status hk_set_product_algorithm(int algorithm);
 
 /* Elementwise primitives on caller-owned DEVICE arrays of `count` numbers of

@@ -32,6 +32,8 @@ EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_
 HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT, HK_PRODUCT_TENSOR = 0, 1, 2, 3
 HK_NTT_AUTO_MIN_M = 8  # include/hk.h: AUTO uses NTT products from 32 * 8 limbs (8192 bits)
 HK_TC_MIN_M = 8        # include/hk.h: tensor-core products exist from 8192 bits
+HK_TC_AUTO_MIN_M = 12  # include/hk.h: AUTO uses them from 12288 bits
+HK_TC_MIN_ROWS = 256   # include/hk.h: steps with fewer trailing rows keep NTT products
 
 
 class Instance(ctypes.Structure):
@@ -44,7 +46,7 @@ class Instance(ctypes.Structure):
                 ("lambda_f64", ctypes.c_double * 3), ("trunc_err_f64", ctypes.c_double * 3),
                 ("seconds", ctypes.c_double), ("status", ctypes.c_int32), ("gamma_nc", ctypes.c_int32),
                 ("message", ctypes.c_char * 128)]
-PROFILE_FIELDS = 10
+PROFILE_FIELDS = 13
 
 
 class HKError(RuntimeError):
@@ -253,7 +255,7 @@ def hk_get_profile(ctx):
     out = np.zeros(PROFILE_FIELDS, np.float64)
     _check(load().hk_get_profile(ctx, _ptr(out, ctypes.c_double), PROFILE_FIELDS), ctx)
     keys = ["launches", "trailing_ms", "trailing_launches", "trailing_limb_macs", "moments_ms", "ldlt_ms",
-            "invblock_ms", "eig_ms", "grad_ms", "scale_ms"]
+            "invblock_ms", "eig_ms", "grad_ms", "scale_ms", "tc_ms", "tc_launches", "tc_mmas"]
     return dict(zip(keys, out.tolist()))
 
 

@@ -68,6 +68,7 @@ struct Ctx {
   uint32_t* tc_p = nullptr;
   size_t tc_db_cap = 0, tc_du_cap = 0, tc_p_cap = 0;  // elements
   double tc_mmas = 0.0;  // tcgen05.mma instructions of the profiled trailing launches
+  std::vector<std::pair<size_t, size_t>> tc_ev;  // events around every tensor-core trailing launch
   // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
   std::map<std::string, DevVec> pool;
   const uint32_t* one_mant = nullptr;  // pool "one" holds 1 while its mant is this (cleared on reallocation)

@@ -753,6 +753,8 @@ hk_status hk_set_profiling(hk_ctx* h, int on) {
   c.scale_ev.clear();
   c.stage_ev.clear();
   c.trail_macs = 0.0;
+  c.tc_ev.clear();
+  c.tc_mmas = 0.0;
   c.launches = 0;
   return HK_OK;
 }
@@ -784,6 +786,13 @@ hk_status hk_get_profile(hk_ctx* h, double* out, int cap) {
     cudaEventElapsedTime(&ms, c.events[p.first], c.events[p.second]);
     out[9] += ms;
   }
+  for (auto& p : c.tc_ev) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c.events[p.first], c.events[p.second]);
+    out[10] += ms;
+  }
+  out[11] = (double)c.tc_ev.size();
+  out[12] = c.tc_mmas;
   return HK_OK;
 }
 

@@ -403,7 +403,10 @@ struct Ops {
           const cudaError_t e = tc_launch(TcTrail<M>{c.A.view(), c.U.view(), N, i}, items, c.tc_db, tc_pitch,
                                           c.tc_du, c.tc_p, tc_g, c.d_err, s);
           if ((st = check_cuda(c, e, "launching the tensor-core update")) != HK_OK) return st;
-          if (c.prof) c.tc_mmas += items * tc_mmas_per_item();
+          if (c.prof) {
+            c.tc_mmas += items * tc_mmas_per_item();
+            c.tc_ev.push_back({e1, prof_mark(c)});
+          }
         } else {
           trailing(i, 1, T);
         }

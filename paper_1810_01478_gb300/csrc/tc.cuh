@@ -70,11 +70,7 @@ struct TcShape {
   static_assert(Z0 - XMAX - 14 >= 0, "staging must cover the lowest Hankel index");
 };
 
-// Steps whose trailing triangle has fewer rows than this keep the NTT kernel
-// (too few 128-row items to fill the GPU).
-#ifndef HK_TC_MIN_ROWS
-#define HK_TC_MIN_ROWS 256
-#endif
+#include "../../include/hk.h"  // HK_TC_MIN_ROWS
 
 constexpr int TC_STAGES = 4;
 constexpr int TC_STAGE_BYTES = 8 * 128 * 16;  // 64 digits x 128 rows of bf16, 8 kgroups of 2 KB
@@ -179,6 +175,43 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // Shared-memory matrix descriptor, no swizzling: start address, leading
 // (K-direction) and stride (M/N-direction) byte offsets between 8 x 16-byte
 // core matrices, and the fixed version bits 46..48 = 0b001.
+// Two 32-column loads (columns at taddr0 and taddr1) and one wait.
+__device__ __forceinline__ void tmem_ld32x2(uint32_t taddr0, uint32_t taddr1, uint32_t (&v)[32], uint32_t (&w)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%64];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+      "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%65];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]),
+        "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+        "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15]),
+        "=r"(w[16]), "=r"(w[17]), "=r"(w[18]), "=r"(w[19]), "=r"(w[20]), "=r"(w[21]), "=r"(w[22]), "=r"(w[23]),
+        "=r"(w[24]), "=r"(w[25]), "=r"(w[26]), "=r"(w[27]), "=r"(w[28]), "=r"(w[29]), "=r"(w[30]), "=r"(w[31])
+      : "r"(taddr0), "r"(taddr1)
+      : "memory");
+}
+
+// acc += sum_u v[31 - u] 2^(7u) for the 32 positions of one group (v holds
+// the group's accumulator columns in reversed order), emitting its 7 limbs;
+// acc keeps the signed carry into the next limb.
+__device__ __forceinline__ void tc_group_limbs(const uint32_t (&v)[32], long long& acc, uint32_t* lim) {
+#pragma unroll
+  for (int u = 0; u < 32; ++u) {
+    const int val = __float2int_rn(__uint_as_float(v[31 - u]));
+    acc += (long long)val * (1ll << ((7 * u) & 31));
+    if (((7 * (u + 1)) >> 5) != ((7 * u) >> 5)) {
+      lim[(7 * u) >> 5] = (uint32_t)acc;
+      acc >>= 32;
+    }
+  }
+}
+
 __device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
          ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
@@ -196,19 +229,34 @@ __device__ __forceinline__ void tc_band(int t, int& lo, int& hi) {
 // column d_tmem: the 16-digit sub-blocks that meet the tile's band.  first:
 // no MMA of the tile issued yet (the first one overwrites the accumulator).
 // Returns the new `first`.
+//
+// The descriptors are formed by addition: the start-address field is the
+// low 14 bits (byte address / 16), so the A descriptor of stage s, sub-block
+// s4 is adesc0 + 1024 s + 256 s4, and the Hankel descriptor of digit k0 is
+// bdesc0 + (k0 - q_hi - XMIN) (core (k0 - q_hi - XMIN) / 8, 128 bytes each),
+// which is >= 0 for every sub-block inside the band.  A K-block wholly inside
+// the band (all but the band's edges) needs no per-sub-block test: this
+// keeps the single issuing thread to a few instructions per MMA.
 template <int M>
-__device__ __forceinline__ bool tc_issue_kblock(uint32_t d_tmem, uint32_t ring_base, uint32_t hc_base, int s, int kb,
+__device__ __forceinline__ bool tc_issue_kblock(uint32_t d_tmem, uint64_t adesc0, uint64_t bdesc0, int s, int kb,
                                                 int t, bool first) {
   using S = TcShape<M>;
   const int q_lo = 256 * t - S::D + 1, q_hi = 256 * t + 255;  // the tile's digit band
+  const uint64_t ad = adesc0 + (uint64_t)(1024 * s);
+  const int k00 = 64 * kb;
+  const uint64_t bd = bdesc0 + (uint64_t)(int64_t)(k00 - q_hi - S::XMIN);
+  if (k00 >= q_lo && k00 + 63 <= q_hi) {
+    tc_mma(d_tmem, ad, bd, TC_IDESC, first ? 0u : 1u);
+    tc_mma(d_tmem, ad + 256, bd + 16, TC_IDESC, 1u);
+    tc_mma(d_tmem, ad + 512, bd + 32, TC_IDESC, 1u);
+    tc_mma(d_tmem, ad + 768, bd + 48, TC_IDESC, 1u);
+    return false;
+  }
 #pragma unroll
   for (int s4 = 0; s4 < 4; ++s4) {
-    const int k0 = 64 * kb + 16 * s4;
+    const int k0 = k00 + 16 * s4;
     if (k0 > q_hi || k0 + 15 < q_lo) continue;
-    const int x0 = k0 - q_hi;  // Hankel argument of core (0, 0); x0 = XMIN (mod 8)
-    const uint64_t ad = tc_sdesc(ring_base + (uint32_t)(s * TC_STAGE_BYTES + s4 * 2 * 2048), 2048, 128);
-    const uint64_t bd = tc_sdesc(hc_base + (uint32_t)(((x0 - S::XMIN) >> 3) * 128), 128, 128);
-    tc_mma(d_tmem, ad, bd, TC_IDESC, first ? 0u : 1u);
+    tc_mma(d_tmem, ad + 256 * s4, bd + 16 * s4, TC_IDESC, first ? 0u : 1u);
     first = false;
   }
   return first;
@@ -516,7 +564,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int s = 0, phase = 0, k = 0;   // ring stage and its phase
       int u0 = 0, u1 = 0;            // uses of accumulators 0 and 1
       bool ok = true;
-      const uint32_t hc_base = smem_u32(hc), ring_base = smem_u32(ring);
+      const uint64_t adesc0 = tc_sdesc(smem_u32(ring), 2048, 128);  // stage 0, sub-block 0
+      const uint64_t bdesc0 = tc_sdesc(smem_u32(hc), 128, 128);      // Hankel core 0 (x = XMIN)
       for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
         if (!mbar_wait(hc_full, k & 1, abort, 3)) break;
         tc_fence_after();
@@ -540,7 +589,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
               }
-              f0 = tc_issue_kblock<M>(tmem, ring_base, hc_base, s, kb, 2 * j, f0);
+              f0 = tc_issue_kblock<M>(tmem, adesc0, bdesc0, s, kb, 2 * j, f0);
               if (kb == hi0) {
                 tc_commit(acc_full);
                 ++u0;
@@ -554,7 +603,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
               }
-              f1 = tc_issue_kblock<M>(tmem + 256u, ring_base, hc_base, s, kb, 2 * j + 1, f1);
+              f1 = tc_issue_kblock<M>(tmem + 256u, adesc0, bdesc0, s, kb, 2 * j + 1, f1);
               if (kb == hi1) {
                 tc_commit(acc_full + 1);
                 ++u1;
@@ -602,22 +651,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         tc_fence_after();
         uint32_t lim[56];
+        // Two independent chains: the tile's low half (groups 0..3, limbs
+        // 0..27, starting from the carry of the previous tile) and its high
+        // half (groups 4..7, limbs 28..55, from zero); the low half's carry
+        // is then added into the high half.  Positions 256t + 32g + u are
+        // columns 255 - 32g - u.
+        long long acc_hi = 0;
+        const uint32_t tcol = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 256);
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          uint32_t v[32];
-          // positions 256t + 32g + u (u = 0..31) are columns 255 - 32g - u
-          tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 256 + 224 - 32 * g), v);
-          // sum_u v_u 2^(7u): limb e of this group is final once 7 (u + 1) reaches 32 (e + 1)
-#pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            const int val = __float2int_rn(__uint_as_float(v[31 - u]));
-            acc += (long long)val * (1ll << ((7 * u) & 31));
-            if (((7 * (u + 1)) >> 5) != ((7 * u) >> 5)) {
-              lim[7 * g + ((7 * u) >> 5)] = (uint32_t)acc;
-              acc >>= 32;
-            }
-          }
+        for (int g = 0; g < 4; ++g) {
+          uint32_t va[32], vb[32];
+          tmem_ld32x2(tcol + (uint32_t)(224 - 32 * g), tcol + (uint32_t)(96 - 32 * g), va, vb);
+          tc_group_limbs(va, acc, lim + 7 * g);
+          tc_group_limbs(vb, acc_hi, lim + 28 + 7 * g);
         }
+#pragma unroll
+        for (int w = 28; w < 56; ++w) {
+          const long long x = (long long)lim[w] + acc;
+          lim[w] = (uint32_t)x;
+          acc = x >> 32;
+        }
+        acc += acc_hi;
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(acc_empty + b);
@@ -646,11 +700,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const uint32_t* pr = pset + (size_t)mm * S::PL;
         TcComb<M> sm(nb);
         const bool p_zero = f.xz || f.yz;
+        // every load of the row in flight at once, then the stores to shared memory
+        uint32_t av[M], pv[2 * M];
+        load_chunk<M>(f.amant, av);
         if (!p_zero) {
-#pragma unroll 8
-          for (int w = 0; w < 2 * M; ++w) sm.sp[IxPad::at(32 * w + lane)] = pr[32 * w + lane];
+#pragma unroll
+          for (int w = 0; w < 2 * M; ++w) pv[w] = __ldcg(pr + 32 * w + lane);
+#pragma unroll
+          for (int w = 0; w < 2 * M; ++w) sm.sp[IxPad::at(32 * w + lane)] = pv[w];
         }
-        copy_to_smem<M, IxPad>(sm.sa, f.amant);
+#pragma unroll
+        for (int w = 0; w < M; ++w) sm.sa[IxPad::at(lane * M + w)] = av[w];
         __syncwarp();
         const bool a_zero = sm.sa[IxPad::at(n - 1)] == 0u;
         uint32_t o[M];

@@ -72,3 +72,13 @@ def test_binding_threshold_matches_header():
     text = open(os.path.join(ROOT, "include", "hk.h")).read()
     m = re.search(r"#define HK_NTT_AUTO_MIN_M (\d+)", text)
     assert m and int(m.group(1)) == hk.HK_NTT_AUTO_MIN_M
+
+
+def test_tensor_core_constants_match_the_header():
+    """The Python binding's copies of the tensor-core thresholds are the header's."""
+    import re
+    import paper_1810_01478_gb300 as hk
+    text = open(os.path.join(ROOT, "include", "hk.h")).read()
+    for name in ("HK_TC_MIN_M", "HK_TC_AUTO_MIN_M", "HK_TC_MIN_ROWS", "HK_PRODUCT_TENSOR"):
+        m = re.search(r"#define %s (\d+)" % name, text)
+        assert m and int(m.group(1)) == getattr(hk, name), name
