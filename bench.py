@@ -13,8 +13,11 @@ on the stream the library runs on.  roofline: the trailing-update kernel
 (Algorithm 1's inner loops): executed modular multiplications of its NTT
 products against the INT32 multiply-add (IMAD) pipe, with the
 schoolbook-equivalent limb-product rate beside it.
-cpu_baseline: the CPU oracle timed on a bounded sample of the same workload.
---impl reference: the oracle arm only (rank 0), same metric and config.
+cpu_baseline: the C++/OpenMP oracle on every host core, timed on a bounded
+sample of the same workload (step 0 of Algorithm 1 at full size) and
+extrapolated by operation count.
+--impl reference: the same oracle as the reference arm (rank 0), same
+metric and config, a smaller sample per step.
 """
 import argparse
 import json
@@ -104,34 +107,65 @@ def ops_count(N, k):
 # ---------------------------------------------------------------------------
 # CPU oracle sample (the reported baseline; never tuned)
 # ---------------------------------------------------------------------------
-def oracle_sample(bits, N, k, budget_s=12.0):
-    """Times the oracle's Algorithm 1 on the leading m x m block of H_N at the
-    same precision (the growing m stops once the budget is used) and
-    extrapolates by operation count to one full solve."""
-    from fractions import Fraction
-    from oracle import moments as OM, ldlt as OL
-    n = bits // 32
-    mu = OM.moments(Fraction(1, 2), N, n)
-    m, spent, last = 8, 0.0, None
-    while True:
-        t0 = time.perf_counter()
-        OL.ldlt_subset(mu, list(range(m)), n)
-        dt = time.perf_counter() - t0
-        spent += dt
-        last = (m, dt)
-        if spent + 2.5 * dt > budget_s or m >= N:
-            break
-        m = int(m * 1.35) + 1
-    m, dt = last
-    fused = (m ** 3 - m) / 6 + 3 * m * (m - 1) / 2     # a quotient costs about 3 fused updates
-    per_op = dt / fused
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or ''."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return ""
+
+
+def cpp_oracle_time(bits, N, cols):
+    """One run of the C++/OpenMP oracle's time mode: step 0 of Algorithm 1
+    on H_N (beta = 1/2) at `bits`, updates of its first `cols` columns."""
+    from oracle import build_cpp
+    exe = build_cpp.build()
+    r = subprocess.run([exe, "time", "2", str(N), str(bits), str(cols)], capture_output=True, text=True,
+                       check=True)
+    return json.loads(r.stdout)
+
+
+def oracle_sample(bits, N, k, budget_s=15.0):
+    """The C++/OpenMP oracle (the paper's A12 loop on every host core) timed
+    on a bounded sample of the same workload: step 0 of Algorithm 1 on the
+    full H_N at the same precision, its N-1 quotients and the updates of its
+    first `cols` columns, `cols` chosen from a short calibration run so the
+    sample takes about budget_s.  Extrapolated by operation count to one
+    solve: the measured cost of a fused update times the fused updates of
+    Algorithm 1, Algorithm 4 and the block, plus the measured cost of a
+    quotient times the quotients (the eigenvalues and gradient, a few percent
+    of the work, are left out)."""
+    cal = cpp_oracle_time(bits, N, 8)
+    per_update = cal["update_seconds"] / max(cal["updates"], 1)
+    m = N - 1
+    cols, acc = 0, 0
+    while cols < m and acc * per_update < budget_s:
+        acc += m - cols
+        cols += 1
+    d = cpp_oracle_time(bits, N, cols)
+    t_u = d["update_seconds"] / d["updates"]
+    t_q = d["scale_seconds"] / d["quotients"]
     tr, qu, a4, bl = ops_count(N, k)
-    solve_s = per_op * (tr + 3 * qu + a4 + bl)
-    return dict(value=3600.0 / solve_s, unit=UNIT, cores=1, kind="oracle",
-                sample=f"oracle Algorithm 1 on the leading {m}x{m} block of H_{N} at {bits} bits "
-                       f"({fused:.3g} fused-update equivalents in {dt:.2f} s), extrapolated by operation count "
-                       f"to one N={N}, k={k} solve ({solve_s:.3g} s)",
-                seconds=round(dt, 2))
+    solve_s = t_u * (tr + a4 + bl) + t_q * qu
+    return dict(value=3600.0 / solve_s, unit=UNIT, cores=d["threads"], kind="oracle",
+                sample=f"C++/OpenMP oracle (oracle/cpp/hk_oracle.cpp, the paper's flattened dynamic-schedule "
+                       f"loop, Sec. 4.3.3) on {d['threads']} host threads: step 0 of Algorithm 1 on the full "
+                       f"H_{N} at {bits} bits, its {d['quotients']} quotients in {d['scale_seconds']:.2f} s and "
+                       f"{d['updates']} fused updates (columns 1..{cols}) in {d['update_seconds']:.2f} s, "
+                       f"extrapolated by operation count to one N={N}, k={k} solve ({solve_s:.4g} s: "
+                       f"{tr + a4 + bl:.4g} fused updates, {qu} quotients; eigenvalues and gradient left out)",
+                extrapolation=(tr + a4 + bl + qu) / (d["updates"] + d["quotients"]),
+                nproc=os.cpu_count(), cpu_model=cpu_model(), seconds=round(d["scale_seconds"] + d["update_seconds"], 2))
 
 
 # ---------------------------------------------------------------------------
@@ -209,13 +243,15 @@ def run_reference(a):
         return
     vals = []
     sample = None
+    budget = max(1.0, min(8.0, 150.0 / max(1, a.warmup + a.steps)))  # the whole run within a few minutes
     for i in range(a.warmup + a.steps):
-        s = oracle_sample(a.bits, a.N, a.k, budget_s=6.0)
+        s = oracle_sample(a.bits, a.N, a.k, budget_s=budget)
         if i >= a.warmup:
             vals.append(s["value"])
             sample = s
     v = statistics.median(vals)
-    cpu = dict(value=v, unit=UNIT, cores=1, kind="oracle", sample=sample["sample"])
+    cpu = dict(value=v, unit=UNIT, cores=sample["cores"], kind="oracle", sample=sample["sample"],
+               nproc=sample["nproc"], cpu_model=sample["cpu_model"], extrapolation=sample["extrapolation"])
     print(json.dumps(dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=a.gpus, steps=a.steps,
                           warmup=a.warmup, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="u32",
                           data="synthetic", config=dict(workload=workload_name(a), N=a.N, k=a.k, bits=a.bits),

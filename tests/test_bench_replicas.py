@@ -98,3 +98,24 @@ def test_trailing_roofline_arithmetic():
     assert r["measured_rates"] is None and r["traffic"] is None
     r = bench.trailing_roofline(prof, 128, False, 152, 2070.0, None, None, None)
     assert r["unit"] == "Tlimb-MAC/s" and r["measured_rates"] is None
+
+
+def test_tensor_roofline_arithmetic():
+    """bench.tensor_roofline: algorithmic flops 2 D^2 per fused update of the
+    tensor-core launches (every step with at least min_rows trailing rows,
+    less its look-ahead entry), times the factorisations profiled, over their
+    device time, against the sustained bf16 peak; the executed rate counts
+    the MMA instructions (128 x 256 x 16 each)."""
+    import bench
+    N, n, min_rows = 300, 768, 256
+    upd = sum((N - 1 - i) * (N - i) // 2 - 1 for i in range(N - 1) if N - 1 - i >= min_rows)
+    assert bench.tc_updates(N, min_rows) == upd
+    D = bench.tc_digits(n)
+    assert D == 3512
+    prof = dict(tc_launches=10, tc_ms=2000.0, tc_mmas=1.0e6)
+    r = bench.tensor_roofline(prof, N, n, min_rows, 100.0, 2)
+    want = 2.0 * D * D * upd * 2 / 2.0 / 1e12
+    assert abs(r["achieved"] - want) < 1e-9 * want
+    assert abs(r["frac"] - want / r["peak"]) < 1e-12
+    assert abs(r["executed_tflops"] - 1.0e6 * 2 * 128 * 256 * 16 / 2.0 / 1e12) < 1e-9
+    assert r["bound"] == "tensor" and abs(r["traffic"] - 100.0 * upd * 2 / 10) < 1e-6
