@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--N", type=int, default=WORKLOAD["N"])
     ap.add_argument("--k", type=int, default=WORKLOAD["k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the rule-width solve and the batched summary after the timed region")
     ap.add_argument("--profile-case", action="store_true",
                     help="only run moments + LDL^T once at --N/--bits (a small case for ncu captures)")
     ap.add_argument("--rows", default="",
@@ -356,6 +358,115 @@ def tensor_roofline(prof, N, n, min_rows, traffic_per_update, solves):
                 schoolbook_equiv_tlimb_macs=upd * n * n / sec / 1e12)
 
 
+def num_fraction(s, e, m):
+    """The exact value of one number of the library's layout."""
+    from fractions import Fraction
+    v = 0
+    for i, w in enumerate(m):
+        v |= int(w) << (32 * i)
+    return Fraction(-v if int(s) else v) * Fraction(2) ** (32 * int(e))
+
+
+def rel_diff_log10(x, y):
+    """log10 |x - y| / |y| of two exact Fractions (-inf when equal)."""
+    import math
+    d = abs(x - y)
+    if d == 0:
+        return float("-inf")
+    q = d / abs(y)
+    return (math.log10(q.numerator) if q.numerator else 0.0) - math.log10(q.denominator)
+
+
+def at_rule_bits(hk, stream, device, a, loss, need, lam_ref, sms, sm_max, rates, steps=4, warmup=2):
+    """The same solve at the width the precision check selects (the least
+    compiled width >= min_bits of hk_precision_loss, which the factor's own
+    loss estimate sets), timed with CUDA events; its lambda_1..3 against the
+    configured-width solve, which has more than twice the bits and so serves
+    as the precision-doubling check; and its trailing-update roofline."""
+    import torch
+    widths = sorted(hk.hk_supported_bits())
+    bits = next(w for w in widths if w >= need)
+    n = bits // 32
+    h = hk.Hankel(device, stream.cuda_stream)
+    try:
+        def solve():
+            h.moments(1, 2, a.N, bits)
+            h.ldlt()
+            h.inv_block(a.k)
+            lam = h.lambda1(3)
+            h.lambda1_grad()
+            return lam
+        for _ in range(warmup):
+            solve()
+        torch.cuda.synchronize()
+        hk.hk_set_profiling(h.ctx, True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            lam = solve()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        prof = hk.hk_get_profile(h.ctx)
+    finally:
+        h.close()
+    diffs = [rel_diff_log10(num_fraction(lam[0][j], lam[1][j], lam[2][j]),
+                            num_fraction(lam_ref[0][j], lam_ref[1][j], lam_ref[2][j])) for j in range(3)]
+    ntt = (bits // 1024) >= hk.HK_NTT_AUTO_MIN_M
+    roof = trailing_roofline(prof, n, ntt, sms, sm_max, rates, None, None)
+    return dict(bits=bits, loss_bits=int(loss), min_bits=int(need), value=solves_per_hour(steps, 1, ms),
+                unit=UNIT, ms_per_solve=ms / steps,
+                lambda_log10_rel_diff_vs_configured_bits=diffs, agree_to_1e40=all(x < -40 for x in diffs),
+                roofline=roof, phases_ms=dict(ldlt=prof["ldlt_ms"] / steps, trailing=prof["trailing_ms"] / steps),
+                note=f"width = least compiled width >= 2 loss + 229 bits (hk_precision_loss); lambda_1..3 compared "
+                     f"with the {a.bits}-bit solve (precision doubling)")
+
+
+def batch_summary(hk, torch, steps=2):
+    """The batched configuration's 16 instances through hk_batch_run
+    (concurrent streams: one context, stream and host thread per instance)
+    against the same instances one after another on one stream."""
+    probs = [dict(beta=(1, m), N=N, k=16, bits=32 * N, n_eig=1) for m in (1, 2, 3, 4) for N in (128, 192, 256, 384)]
+    t = batch_times(hk, torch, probs, steps, 1)
+    return dict(instances=len(probs), form="concurrent streams (one context, stream and host thread per instance), "
+                                           "not one persistent launch",
+                workload="beta=1/m, m in {1,2,3,4} x N in {128,192,256,384}, k=16, 32N bits, moments -> LDL^T -> "
+                         "block -> lambda_1",
+                seconds_batched=t["batched"], seconds_sequential=t["sequential"],
+                speedup=t["sequential"] / t["batched"], instances_per_hour=3600.0 * len(probs) / t["batched"])
+
+
+def batch_times(hk, torch, probs, steps, warmup):
+    """Wall seconds per pass of hk_batch_run over probs and of the same
+    instances solved one after another on one stream."""
+    def batched():
+        st, res = hk.hk_batch_run(0, probs, max_concurrent=len(probs))
+        assert st == hk.HK_OK, [r["message"] for r in res if r["status"]]
+        return res
+
+    def sequential():
+        out = []
+        for p in probs:
+            with hk.Hankel(0) as h:
+                h.moments(*p["beta"], p["N"], p["bits"])
+                h.ldlt()
+                h.inv_block(p["k"])
+                out.append(h.lambda1(1))
+        return out
+
+    for _ in range(max(1, warmup)):
+        batched()
+    torch.cuda.synchronize()
+    times = {}
+    for name, fn in (("batched", batched), ("sequential", sequential)):
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            fn()
+        torch.cuda.synchronize()
+        times[name] = (time.perf_counter() - t0) / steps
+    return times
+
+
 def run_ours(a):
     import torch
     ws, rank, local = dist_env()
@@ -459,6 +570,10 @@ def run_ours(a):
                               trailing_tensor=prof["tc_ms"] / a.steps),
                result=dict(lambda_f64=lam_f64, trunc_err_f64=lam[4].tolist(), dlambda_dbeta_f64=gr[3].tolist()[0]),
                clocks=clk)
+    if rank == 0 and ws == 1 and not a.no_side:
+        loss, need = h.precision_loss()
+        out["at_rule_bits"] = at_rule_bits(hk, stream, local, a, loss, need, lam, sms, sm_max, rates)
+        out["batch"] = batch_summary(hk, torch)
     if rank == 0 and ws == 1 and not a.no_cpu_baseline:
         out["cpu_baseline"] = oracle_sample(a.bits, a.N, a.k)
     h.close()
@@ -489,50 +604,20 @@ def profile_case(a):
 
 
 def run_batch(a):
-    """The batched form: 16 instances of uneven size in one hk_batch_run (one
-    context, stream and host thread each), timed beside the same instances
-    solved one after another on one stream.  beta = 1/m (moments exact on the
-    device) with m in {1, 2, 3, 4}, N in {128, 192, 256, 384}, k = 16,
-    32 N bits: the shapes of the paper-scale batched configuration."""
+    """The batched form alone: 16 instances of uneven size through
+    hk_batch_run (concurrent streams: one context, stream and host thread
+    each), timed beside the same instances solved one after another on one
+    stream.  beta = 1/m (moments exact on the device) with m in {1, 2, 3, 4},
+    N in {128, 192, 256, 384}, k = 16, 32 N bits: the shapes of the
+    paper-scale batched configuration."""
     import torch
     import __graft_entry__ as g
     g.build()
     import paper_1810_01478_gb300 as hk
-    probs = [dict(beta=(1, m), N=N, k=16, bits=32 * N, n_eig=1) for m in (1, 2, 3, 4) for N in (128, 192, 256, 384)]
-
-    def batched():
-        st, res = hk.hk_batch_run(0, probs, max_concurrent=len(probs))
-        assert st == hk.HK_OK, [r["message"] for r in res if r["status"]]
-        return res
-
-    def sequential():
-        out = []
-        for p in probs:
-            with hk.Hankel(0) as h:
-                h.moments(*p["beta"], p["N"], p["bits"])
-                h.ldlt()
-                h.inv_block(p["k"])
-                out.append(h.lambda1(1))
-        return out
-
-    for _ in range(max(1, a.warmup)):
-        batched()
-    torch.cuda.synchronize()
-    times = {}
-    for name, fn in (("batched", batched), ("sequential", sequential)):
-        t0 = time.perf_counter()
-        for _ in range(a.steps):
-            fn()
-        torch.cuda.synchronize()
-        times[name] = (time.perf_counter() - t0) / a.steps
-    per_hour = 3600.0 * len(probs) / times["batched"]
-    print(json.dumps(dict(metric="instances/hour (16 uneven lambda_1 solves, batched)", value=per_hour,
-                          unit="instances/hour", n_gpus=1, steps=a.steps, warmup=a.warmup,
-                          higher_is_better=True, data="synthetic",
-                          config=dict(workload="batch: beta=1/m, m in {1,2,3,4} x N in {128,192,256,384}, k=16, "
-                                               "32N bits, moments -> LDL^T -> block -> lambda_1"),
-                          seconds_batched=times["batched"], seconds_sequential=times["sequential"],
-                          speedup=times["sequential"] / times["batched"])), flush=True)
+    out = batch_summary(hk, torch, steps=a.steps)
+    print(json.dumps(dict(metric="instances/hour (16 uneven lambda_1 solves, concurrent streams)",
+                          value=out["instances_per_hour"], unit="instances/hour", n_gpus=1, steps=a.steps,
+                          warmup=a.warmup, higher_is_better=True, data="synthetic", **out)), flush=True)
 
 
 def run_table2(a):

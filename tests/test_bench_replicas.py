@@ -119,3 +119,15 @@ def test_tensor_roofline_arithmetic():
     assert abs(r["frac"] - want / r["peak"]) < 1e-12
     assert abs(r["executed_tflops"] - 1.0e6 * 2 * 128 * 256 * 16 / 2.0 / 1e12) < 1e-9
     assert r["bound"] == "tensor" and abs(r["traffic"] - 100.0 * upd * 2 / 10) < 1e-6
+
+
+def test_exact_lambda_comparison_helpers():
+    """bench.num_fraction reads the library's number layout exactly, and
+    bench.rel_diff_log10 gives log10 of the relative difference."""
+    import bench
+    from fractions import Fraction
+    assert bench.num_fraction(1, -1, [0, 3]) == Fraction(-3)
+    assert bench.num_fraction(0, 2, [5]) == Fraction(5 * 2 ** 64)
+    x, y = Fraction(1) + Fraction(1, 10 ** 45), Fraction(1)
+    assert -45.01 < bench.rel_diff_log10(x, y) < -44.99
+    assert bench.rel_diff_log10(y, y) == float("-inf")
