@@ -658,15 +658,24 @@ def run_table2(a):
                               trunc_err_f64=[float(v) for v in terr], trunc_err_printed=row["trunc_err"])),
               flush=True)
     if len(pts) >= 2:
-        xs = [math.log(4 * math.pi * N * math.e) for N, _ in pts]
-        ys = [math.log(8 * math.pi * math.sqrt(math.log(N)) / l1) for N, l1 in pts]
-        ws = [N * N for N, _ in pts]
-        sw = sum(ws)
-        mx = sum(w * x for w, x in zip(ws, xs)) / sw
-        my = sum(w * y for w, y in zip(ws, ys)) / sw
-        b = sum(w * (x - mx) * (y - my) for w, x, y in zip(ws, xs, ys)) / sum(w * (x - mx) ** 2 for w, x in zip(ws, xs))
-        print(json.dumps(dict(workload="table2_fit", rows=[N for N, _ in pts], intercept=my - b * mx, slope=b,
+        a0, b = sec61_fit(pts)
+        print(json.dumps(dict(workload="table2_fit", rows=[N for N, _ in pts], intercept=a0, slope=b,
                               paper=table["fit"])), flush=True)
+
+
+def sec61_fit(pts):
+    """Sec. 6.1's fit on (N, lambda_1) points: the N^2-weighted least-squares
+    line y = a + b x with x = log(4 pi N e) and y = log(8 pi sqrt(log N) /
+    lambda_1); returns (a, b).  The paper reads b against 2/pi."""
+    import math
+    xs = [math.log(4 * math.pi * N * math.e) for N, _ in pts]
+    ys = [math.log(8 * math.pi * math.sqrt(math.log(N)) / l1) for N, l1 in pts]
+    ws = [N * N for N, _ in pts]
+    sw = sum(ws)
+    mx = sum(w * x for w, x in zip(ws, xs)) / sw
+    my = sum(w * y for w, y in zip(ws, ys)) / sw
+    b = sum(w * (x - mx) * (y - my) for w, x, y in zip(ws, xs, ys)) / sum(w * (x - mx) ** 2 for w, x in zip(ws, xs))
+    return my - b * mx, b
 
 
 def local_slopes(pts, xf):

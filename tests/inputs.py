@@ -101,3 +101,16 @@ def measure_moments(seed, N, atoms=None, w_bits=20, t_max=None):
     nodes = rng.sample(range(1, t_max + 1), atoms)
     weights = [rng.randint(1, 1 << w_bits) for _ in range(atoms)]
     return [sum(w * t ** j for w, t in zip(weights, nodes)) for j in range(2 * N - 1)]
+
+
+def near_degenerate_moments(d):
+    """mu_0..mu_4 of the measure with weights 10^6, 2 10^6, 12 10^6 + d,
+    2 10^6, 10^6 at the nodes -2, -1, 0, 1, 2.  For N = 3 its Hankel matrix
+    has eigenvalues 12 10^6 (twice) and 42 10^6 when d = 0 (the odd moments
+    vanish, so e_2 is an eigenvector with eigenvalue mu_2, and
+    (mu_0 - mu_2)(mu_4 - mu_2) = mu_2^2 puts mu_2 in the spectrum of the outer
+    2 x 2 block too); d > 0 splits the pair (d = 1: relative gap 7e-8;
+    d = 24: 1.6e-6)."""
+    nodes = (-2, -1, 0, 1, 2)
+    weights = (10 ** 6, 2 * 10 ** 6, 12 * 10 ** 6 + d, 2 * 10 ** 6, 10 ** 6)
+    return [sum(w * t ** j for w, t in zip(weights, nodes)) for j in range(5)]

@@ -131,3 +131,17 @@ def test_exact_lambda_comparison_helpers():
     x, y = Fraction(1) + Fraction(1, 10 ** 45), Fraction(1)
     assert -45.01 < bench.rel_diff_log10(x, y) < -44.99
     assert bench.rel_diff_log10(y, y) == float("-inf")
+
+
+def test_sec61_fit_reproduces_the_printed_coefficients():
+    """bench.sec61_fit on Table 2's printed lambda_1 column (Sec. 5.1) gives
+    the coefficients Sec. 6.1 prints, 0.04630 and 0.63646 (the slope within
+    the printed 95 % interval [0.63510, 0.63781], which holds 2/pi)."""
+    import json
+    import math
+    import bench
+    t = json.load(open(os.path.join(ROOT, "tests", "golden", "table2_beta_half.json")))
+    pts = [(r["N"], float(r["lambda"][0])) for r in t["rows"]]
+    a, b = bench.sec61_fit(pts)
+    assert round(a, 5) == float(t["fit"]["intercept"]) and round(b, 5) == float(t["fit"]["slope"])
+    assert 0.63510 <= b <= 0.63781 and 0.63510 <= 2 / math.pi <= 0.63781

@@ -171,3 +171,25 @@ def test_degenerate_sizes_vs_oracle(N, k, n_eig, bits):
                     assert abs(terr[j] - float(want_t)) <= 1e-6 * abs(float(want_t))
     finally:
         h.close()
+
+
+@pytest.mark.parametrize("d", [24, 1, 0])
+def test_near_degenerate_top_eigenvalues(d):
+    """S = H_3^{-1} with its two largest eigenvalues equal (d = 0) or split by
+    7e-8 (d = 1) and 1.6e-6 (d = 24), relative: the repeated squaring needs
+    up to about 33 squarings there, and the deflated second eigenvalue sits
+    on top of the first.  lambda_1..3 against the oracle to 1e-40."""
+    import paper_1810_01478_gb300 as hk
+    N = k = 3
+    bits = 1024
+    n = bits // 32
+    mu = [F.from_int(v, n) for v in inputs.near_degenerate_moments(d)]
+    ref = PL.run(None, N, k, n, mu=mu)
+    h, lam, _ = run_path(hk, (0, 0), N, k, bits, mu=mu, n_eig=3)
+    try:
+        with mpm.workprec(ref["prec"]):
+            for j in range(3):
+                got = gpu_mpf(lam[0][j], lam[1][j], lam[2][j])
+                assert abs(got - ref["lambdas"][j]) / ref["lambdas"][j] < LAMBDA_TOL, (d, j)
+    finally:
+        h.close()

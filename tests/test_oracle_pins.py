@@ -341,3 +341,21 @@ def test_loss_estimate_bounds_the_doubling_loss(m, N, n):
             lost = max(lost, 32 * n + float(mpm.log(d, 2)))
     assert est > 0 and lost > est                     # the estimate is a proxy, not the loss
     assert lost <= PR.LOSS_FACTOR * est + PR.LOSS_SLACK
+
+
+def test_degenerate_spectrum_closed_form():
+    """A Hankel matrix with a double smallest eigenvalue
+    (tests/inputs.near_degenerate_moments(0): mu = 18e6, 0, 12e6, 0, 36e6)
+    has the spectrum {12e6, 12e6, 42e6} in closed form.  With N = k = 3 the
+    block S is all of H^{-1}, whose eigenvalues nu are the reciprocals, so
+    lambda_m = 1/nu_m must be 12e6, 12e6 and 42e6: the oracle's eigensolve
+    and its deflation hold at an exactly repeated top eigenvalue of S."""
+    from oracle import pipeline as PL
+    n = 32
+    mu = [F.from_int(v, n) for v in inputs.near_degenerate_moments(0)]
+    assert [F.to_fraction(x) for x in mu] == [18 * 10 ** 6, 0, 12 * 10 ** 6, 0, 36 * 10 ** 6]
+    r = PL.run(None, 3, 3, n, mu=mu)
+    with mpm.workprec(r["prec"]):
+        want = [mpm.mpf(12 * 10 ** 6), mpm.mpf(12 * 10 ** 6), mpm.mpf(42 * 10 ** 6)]
+        for got, w in zip(r["lambdas"], want):
+            assert abs(got - w) / w < mpm.mpf(10) ** -250
