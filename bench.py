@@ -684,17 +684,70 @@ def local_slopes(pts, xf):
     return [(math.log(l1) - math.log(l0)) / (xf(n1) - xf(n0)) for (n0, l0), (n1, l1) in zip(pts, pts[1:])]
 
 
+def gamma_constants_limbs(a, b):
+    """The constants Gamma(r/a), r = 1..a-1, for hk_moments_gamma, from
+    tests/golden/c3_gamma_constants.json (12416 correct bits, written there
+    by the repository's golden-value script): (limb exponents, limbs)."""
+    import numpy as np
+    from fractions import Fraction
+    d = json.load(open(os.path.join(ROOT, "tests", "golden", "c3_gamma_constants.json")))
+    raw = d["constants"][f"{a}/{b}"]
+    vals = [Fraction(int(p, 16), int(q, 16)) for p, q in raw[1:]]
+    rows, exps = [], []
+    for v in vals:
+        s = v.denominator.bit_length() - 1
+        e = -((s + 31) // 32)
+        rows.append(v.numerator << (32 * -e - s))
+        exps.append(e)
+    nc = max((m.bit_length() + 31) // 32 for m in rows)
+    limbs = np.zeros((len(rows), nc), np.uint32)
+    for i, m in enumerate(rows):
+        sh = nc - (m.bit_length() + 31) // 32
+        m <<= 32 * sh
+        exps[i] -= sh
+        for k in range(nc):
+            limbs[i, k] = (m >> (32 * k)) & 0xFFFFFFFF
+    return np.array(exps, np.int32), limbs
+
+
+def limit_fit(pts):
+    """beta < 1/2: lambda_1(N) -> lambda_inf > 0.  On three points at doubling
+    N, lambda(N) = lambda_inf + C N^-p is determined exactly (Aitken's delta^2
+    on the geometric sequence of differences): returns (lambda_inf, p)."""
+    import math
+    (n0, l0), (n1, l1), (n2, l2) = pts[-3:]
+    assert n1 == 2 * n0 and n2 == 2 * n1
+    d0, d1 = l1 - l0, l2 - l1
+    r = d1 / d0
+    return l2 + d1 * r / (1 - r), -math.log2(r)
+
+
+def sqrt_decay_fit(pts):
+    """beta > 1/2: Szego's form for the Laguerre weight (beta = 1, Sec. 1),
+    lambda_1 ~ A N^(1/4) B^sqrt(N): least squares of log lambda_1 - log(N)/4
+    on sqrt(N); returns (log A, log B).  Also the effective exponent gamma
+    of -log lambda_1 ~ c N^gamma from the last two points."""
+    import math
+    xs = [math.sqrt(N) for N, _ in pts]
+    ys = [math.log(l) - 0.25 * math.log(N) for N, l in pts]
+    mx, my = sum(xs) / len(xs), sum(ys) / len(ys)
+    b = sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sum((x - mx) ** 2 for x in xs)
+    (n0, l0), (n1, l1) = pts[-2:]
+    gamma = (math.log(-math.log(l1)) - math.log(-math.log(l0))) / (math.log(n1) - math.log(n0))
+    return my - b * mx, b, gamma
+
+
 def run_regimes(a):
-    """The three regimes of the weight exp(-x^beta) (abstract, Sec. 1 and 6):
-    lambda_1 bounded below for beta < 1/2 (indeterminate moment problem),
-    algebraic decay at beta = 1/2, exponential decay for beta > 1/2; shown at
-    beta = 1/3, 1/2, 1 (exact moments) for N = 128 ... 1024, k = 64 (at
-    beta = 1 and N = 1024 a k = 32 block still has a 30 % truncation
-    estimate; k = 64 brings every row below 1e-20).  Each
-    solve runs at the least compiled width the precision check accepts
-    (hk_precision_loss, tried from a width of 2 N + 229 bits up).  One JSON
-    line per solve, then one per beta with the local slopes of log lambda_1
-    against log N and against sqrt(N)."""
+    """The three regimes of the weight exp(-x^beta) (abstract, Sec. 1 and 6)
+    at beta = 1/3, 9/20 (< 1/2: indeterminate moment problem, lambda_1
+    bounded below), 1/2 (algebraic decay), 11/20 and 1 (> 1/2: exponential
+    decay), N = 128 ... 1024, k = 64 (at beta = 1 and N = 1024 a k = 32 block
+    still has a 30 % truncation estimate).  beta = 1/m uses the device's
+    exact moments, beta = 9/20, 11/20 the constants Gamma(r/20) (12416 bits).
+    Each solve runs at the least compiled width the precision check accepts
+    (hk_precision_loss, tried from 2 N + 229 bits up).  One JSON line per
+    solve, then one per beta with its fit: the limit lambda_inf (beta < 1/2),
+    Sec. 6.1's exponent (beta = 1/2), Szego's sqrt(N) decay rate (beta > 1/2)."""
     import math
     import torch
     import __graft_entry__ as g
@@ -702,7 +755,8 @@ def run_regimes(a):
     import paper_1810_01478_gb300 as hk
     widths = sorted(hk.hk_supported_bits())
     Ns = [int(x) for x in a.rows.split(",") if x] if a.rows else [128, 256, 512, 1024]
-    for m in (3, 2, 1):
+    for bn, bd in ((1, 3), (9, 20), (1, 2), (11, 20), (1, 1)):
+        consts = gamma_constants_limbs(bn, bd) if bn > 1 else None
         pts = []
         for N in Ns:
             k = min(64, N)
@@ -712,7 +766,10 @@ def run_regimes(a):
             while True:
                 h = hk.Hankel(0)
                 try:
-                    h.moments(1, m, N, bits)
+                    if consts is None:
+                        h.moments(bn, bd, N, bits)
+                    else:
+                        h.moments_gamma(bn, bd, N, bits, *consts)
                     h.ldlt()
                     loss, need = h.precision_loss()
                     if need > bits and bits < widths[-1]:
@@ -725,12 +782,25 @@ def run_regimes(a):
                     h.close()
             dt = time.perf_counter() - t0
             pts.append((N, float(lam[0])))
-            print(json.dumps(dict(workload="regimes", beta=f"1/{m}", N=N, k=k, bits=bits, loss_bits=loss,
+            print(json.dumps(dict(workload="regimes", beta=f"{bn}/{bd}", N=N, k=k, bits=bits, loss_bits=loss,
                                   seconds=dt, lambda_f64=[float(v) for v in lam],
                                   trunc_err_f64=[float(v) for v in terr])), flush=True)
-        print(json.dumps(dict(workload="regimes_slopes", beta=f"1/{m}", N=Ns,
-                              dlog_lambda_dlog_N=local_slopes(pts, math.log),
-                              dlog_lambda_dsqrt_N=local_slopes(pts, math.sqrt))), flush=True)
+        fit = dict(workload="regimes_fit", beta=f"{bn}/{bd}", N=Ns,
+                   dlog_lambda_dlog_N=local_slopes(pts, math.log),
+                   dlog_lambda_dsqrt_N=local_slopes(pts, math.sqrt))
+        if 2 * bn < bd and len(pts) >= 3:
+            li, pw = limit_fit(pts)
+            fit.update(lambda_inf=li, approach_exponent=pw,
+                       model="lambda_1 = lambda_inf + C N^-p through the last three points (doubling N)")
+        elif 2 * bn == bd and len(pts) >= 2:
+            a0, b0 = sec61_fit(pts)
+            fit.update(sec61_intercept=a0, sec61_slope=b0, two_over_pi=2 / math.pi,
+                       model="Sec. 6.1: N^2-weighted y = a + b x, x = log(4 pi N e), y = log(8 pi sqrt(log N)/lambda_1)")
+        elif len(pts) >= 2:
+            la, lb, gam = sqrt_decay_fit(pts)
+            fit.update(log_A=la, log_B=lb, B=math.exp(lb), effective_exponent=gam,
+                       model="Szego (beta = 1): lambda_1 ~ A N^(1/4) B^sqrt(N); -log lambda_1 ~ c N^gamma")
+        print(json.dumps(fit), flush=True)
 
 
 if __name__ == "__main__":

@@ -14,7 +14,7 @@ asked) and stores, in tests/golden/<name>.json:
 Usage:  python tests/golden/make_golden.py <target> [<target> ...]
 Targets: c1, c2, c5_512_4096, c5_768_4096, c5_1024_4096, c5_1024_8192,
          w_256_24576, w_160_16384, w_320_24576 (whole factors at 24576 and
-         16384 bits),
+         16384 bits), r_<a>_<b>_<N> (beta = a/b at N = 128, 256: the regimes),
          c3const (Gamma(r/a) constants for beta = 9/20, 11/20),
          c3_<a>_<b>_<N> (one batched-config instance; beta = a/b, k = 16,
          bits = 32 N, non-dyadic moments from the stored constants)
@@ -46,6 +46,11 @@ TARGETS = {
     "w_160_16384": dict(beta=(1, 2), N=160, k=32, bits=16384, grad=True, fd=False),
     # N > 256: the first steps of Algorithm 1 have at least 256 trailing rows
     "w_320_24576": dict(beta=(1, 2), N=320, k=32, bits=24576, grad=False, fd=False),
+    # the regimes of the weight away from beta = 1/2 (k = 64, as bench.py --workload regimes)
+    "r_1_3_128": dict(beta=(1, 3), N=128, k=64, bits=2048, grad=False, fd=False),
+    "r_1_3_256": dict(beta=(1, 3), N=256, k=64, bits=2048, grad=False, fd=False),
+    "r_1_1_128": dict(beta=(1, 1), N=128, k=64, bits=2048, grad=False, fd=False),
+    "r_1_1_256": dict(beta=(1, 1), N=256, k=64, bits=2048, grad=False, fd=False),
 }
 
 

@@ -145,3 +145,17 @@ def test_sec61_fit_reproduces_the_printed_coefficients():
     a, b = bench.sec61_fit(pts)
     assert round(a, 5) == float(t["fit"]["intercept"]) and round(b, 5) == float(t["fit"]["slope"])
     assert 0.63510 <= b <= 0.63781 and 0.63510 <= 2 / math.pi <= 0.63781
+
+
+def test_regime_fits_recover_their_models():
+    """bench.limit_fit recovers lambda_inf and p of lambda_inf + C N^-p from
+    three doubling points; bench.sqrt_decay_fit recovers log A and log B of
+    A N^(1/4) B^sqrt(N)."""
+    import math
+    import bench
+    pts = [(n, 3.3 + 2.0 * n ** -0.55) for n in (256, 512, 1024)]
+    li, p = bench.limit_fit(pts)
+    assert abs(li - 3.3) < 1e-9 and abs(p - 0.55) < 1e-9
+    pts = [(n, math.exp(-1.5) * n ** 0.25 * math.exp(-4.0 * math.sqrt(n))) for n in (128, 256, 512, 1024)]
+    la, lb, gam = bench.sqrt_decay_fit(pts)
+    assert abs(la + 1.5) < 1e-9 and abs(lb + 4.0) < 1e-9 and 0.4 < gam < 0.6
