@@ -202,8 +202,10 @@ HK_API hk_status hk_export(hk_ctx* ctx, int what, int64_t first, int64_t count, 
  *   [9] column scale (B_i) and its transforms within the LDL^T, ms
  *   [10] device time of the trailing-update launches with tensor-core
  *        products (included in [1]), ms; [11] their number; [12] the
- *        tcgen05.mma instructions they issued (M = 128, N = 256, K = 16 each) */
-#define HK_PROFILE_FIELDS 13
+ *        tcgen05.mma instructions they issued (M = 128, N = 256, K = 16 each)
+ *   [13] 128-row items whose short products left a row undecided, re-run
+ *        with whole products (their instructions are included in [12]) */
+#define HK_PROFILE_FIELDS 14
 HK_API hk_status hk_set_profiling(hk_ctx* ctx, int on);
 HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 

@@ -46,7 +46,7 @@ class Instance(ctypes.Structure):
                 ("lambda_f64", ctypes.c_double * 3), ("trunc_err_f64", ctypes.c_double * 3),
                 ("seconds", ctypes.c_double), ("status", ctypes.c_int32), ("gamma_nc", ctypes.c_int32),
                 ("message", ctypes.c_char * 128)]
-PROFILE_FIELDS = 13
+PROFILE_FIELDS = 14
 
 
 class HKError(RuntimeError):
@@ -255,7 +255,8 @@ def hk_get_profile(ctx):
     out = np.zeros(PROFILE_FIELDS, np.float64)
     _check(load().hk_get_profile(ctx, _ptr(out, ctypes.c_double), PROFILE_FIELDS), ctx)
     keys = ["launches", "trailing_ms", "trailing_launches", "trailing_limb_macs", "moments_ms", "ldlt_ms",
-            "invblock_ms", "eig_ms", "grad_ms", "scale_ms", "tc_ms", "tc_launches", "tc_mmas"]
+            "invblock_ms", "eig_ms", "grad_ms", "scale_ms", "tc_ms", "tc_launches", "tc_mmas",
+            "tc_redo_items"]
     return dict(zip(keys, out.tolist()))
 
 

@@ -67,7 +67,12 @@ struct Ctx {
   uint16_t* tc_du = nullptr;
   uint32_t* tc_p = nullptr;
   size_t tc_db_cap = 0, tc_du_cap = 0, tc_p_cap = 0;  // elements
-  double tc_mmas = 0.0;  // tcgen05.mma instructions of the profiled trailing launches
+  // undecided rows of the short-product launches: count, running total of
+  // re-run items, then per-item records (Ops::tc_redo_ints)
+  int* tc_redo = nullptr;
+  size_t tc_redo_ints = 0;
+  double tc_mmas = 0.0;  // tcgen05.mma instructions of the profiled trailing launches (first launches)
+  double tc_mmas_whole = 0.0;  // ... of one item of a re-run launch (whole product)
   std::vector<std::pair<size_t, size_t>> tc_ev;  // events around every tensor-core trailing launch
   // named scratch arrays of the later stages (grown on demand, freed in hk_destroy)
   std::map<std::string, DevVec> pool;

@@ -375,6 +375,7 @@ void hk_destroy(hk_ctx* h) {
   if (c.tc_db) cudaFree(c.tc_db);
   if (c.tc_du) cudaFree(c.tc_du);
   if (c.tc_p) cudaFree(c.tc_p);
+  if (c.tc_redo) cudaFree(c.tc_redo);
   if (c.d_err) cudaFree(c.d_err);
   delete h;
 }
@@ -755,6 +756,7 @@ hk_status hk_set_profiling(hk_ctx* h, int on) {
   c.trail_macs = 0.0;
   c.tc_ev.clear();
   c.tc_mmas = 0.0;
+  if (c.tc_redo && (st = check_cuda(c, cudaMemset(c.tc_redo + 1, 0, sizeof(int)), "clearing")) != HK_OK) return st;
   c.launches = 0;
   return HK_OK;
 }
@@ -791,8 +793,13 @@ hk_status hk_get_profile(hk_ctx* h, double* out, int cap) {
     cudaEventElapsedTime(&ms, c.events[p.first], c.events[p.second]);
     out[10] += ms;
   }
+  int redo = 0;
+  if (c.tc_redo && (st = check_cuda(c, cudaMemcpy(&redo, c.tc_redo + 1, sizeof(int), cudaMemcpyDeviceToHost),
+                                    "reading the re-run count")) != HK_OK)
+    return st;
   out[11] = (double)c.tc_ev.size();
-  out[12] = c.tc_mmas;
+  out[12] = c.tc_mmas + redo * c.tc_mmas_whole;
+  out[13] = (double)redo;
   return HK_OK;
 }
 

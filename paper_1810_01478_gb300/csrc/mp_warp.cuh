@@ -315,6 +315,9 @@ __device__ __forceinline__ void frame_chunk(const Staged& s, int c, uint32_t (&v
 struct Result {
   int sgn, exp;
   bool zero;
+  // a short product's truncation is not determined (nothing was written to
+  // out; the caller recomputes the entry with the whole product)
+  bool amb = false;
 };
 
 // trunc_n( sX*|X| + sY*|Y| ), sX/sY in {0:+, 1:-}, frame limb 0 having weight
@@ -328,9 +331,19 @@ struct Result {
 // between 0 and the larger operand's last-limb weight gives the same
 // truncated result (the larger one is a multiple of that weight, and the
 // result's own last limb is at most one limb lower), so the stand-in is exact.
-template <int M, class IX = IxPlain>
+//
+// Short products (CUT, chk >= 0): Y holds P~, a product without its terms
+// below some position, and the exact sum differs from the frame's by less
+// than the weight of frame limb chk.  The truncation of the exact sum is the
+// frame's when the frame limbs from chk up to the result's last limb hold
+// one limb that is not 0 and one that is not all ones: then the remainder
+// below the result's last limb is at least that weight and at most the last
+// limb's weight minus it, so no perturbation smaller than chk's weight can
+// carry or borrow across the last limb or change the leading limb.
+// Otherwise (also for a zero frame) the result is flagged amb and not formed.
+template <int M, class IX = IxPlain, bool CUT = false>
 __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged& Y, int sY, int base,
-                                          uint32_t* fr, uint32_t (&out)[M]) {
+                                          uint32_t* fr, uint32_t (&out)[M], int chk = -1) {
   constexpr int n = 32 * M;
   const int lane = lane_id();
   uint32_t r[3][M];
@@ -405,6 +418,7 @@ __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged&
 #pragma unroll
     for (int k = 0; k < M; ++k) out[k] = 0;
     res.sgn = 0; res.exp = 0; res.zero = true;
+    if (CUT && chk >= 0) res.amb = true;
     return res;
   } else {
     const int h = top_bit128(NZ);
@@ -415,6 +429,27 @@ __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged&
     else kk = chunk_top<M>(r[2]);
     kk = __shfl_sync(FULL, kk, src);
     T = h * M + kk;
+  }
+  if constexpr (CUT) {
+    if (chk >= 0) {
+      const int last = T - n + 1;
+      bool nz = false, nf = false;
+#pragma unroll
+      for (int grp = 0; grp < 3; ++grp)
+#pragma unroll
+        for (int k = 0; k < M; ++k) {
+          const int f = (grp * 32 + lane) * M + k;
+          if (f >= chk && f < last) {
+            nz |= r[grp][k] != 0u;
+            nf |= r[grp][k] != 0xFFFFFFFFu;
+          }
+        }
+      if (!__any_sync(FULL, nz) || !__any_sync(FULL, nf)) {
+        res.sgn = 0; res.exp = 0; res.zero = false;
+        res.amb = true;
+        return res;
+      }
+    }
   }
   __syncwarp();
 #pragma unroll
@@ -429,6 +464,97 @@ __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged&
     const int i = lowest + lane * M + k;
     out[k] = (i >= 0) ? fr[IX::at(i)] : 0u;
   }
+  __syncwarp();
+  res.sgn = rs;
+  res.exp = base + lowest;
+  res.zero = false;
+  return res;
+}
+
+// combine() on a frame of one chunk of MC limbs per lane (32 MC limbs,
+// n = 32 M < 32 MC), for operands that both lie inside it, with the
+// short-product test always on (chk >= 1, see combine()).  The carry or
+// borrow between the lanes' chunks is resolved with one 32-bit ballot per
+// kind and a 64-bit prefix sum whose bit 32 is the carry out of the frame.
+template <int MC, int M, class IX>
+__device__ __forceinline__ Result combine_narrow(const Staged& X, int sX, const Staged& Y, int sY, int base,
+                                                 uint32_t* fr, uint32_t (&out)[M], int chk) {
+  constexpr int n = 32 * M, W = 32 * MC;
+  static_assert(MC > M, "the frame must be wider than a result");
+  const int lane = lane_id();
+  uint32_t r[MC];
+  uint32_t top = 0;
+  int rs = sX;
+  {
+    uint32_t xv[MC], yv[MC];
+    frame_chunk<MC, IX>(X, lane, xv);
+    frame_chunk<MC, IX>(Y, lane, yv);
+    if (sX == sY) {
+      const bool g = chunk_add<MC>(r, xv, yv) != 0;
+      const bool p = !g && chunk_is_ones<MC>(r);
+      const uint64_t G = __ballot_sync(FULL, g), A = G | __ballot_sync(FULL, p);
+      const uint64_t C = (A + G) ^ A ^ G;  // carry into chunk l is bit l, out of the frame bit 32
+      if ((C >> lane) & 1) chunk_add_word<MC>(r, 1u);
+      top = (uint32_t)(C >> 32) & 1u;
+    } else {
+      const bool g = chunk_sub<MC>(r, xv, yv) != 0;
+      const bool p = !g && chunk_is_zero<MC>(r);
+      const uint64_t G = __ballot_sync(FULL, g), A = G | __ballot_sync(FULL, p);
+      const uint64_t B = (A + G) ^ A ^ G;  // borrow into chunk l is bit l
+      if ((B >> lane) & 1) chunk_dec<MC>(r);
+      if ((B >> 32) & 1) {
+        // |X| < |Y|: negate the frame's two's complement value
+#pragma unroll
+        for (int k = 0; k < MC; ++k) r[k] = ~r[k];
+        const uint32_t O = __ballot_sync(FULL, chunk_is_ones<MC>(r));
+        const uint32_t notO = ~O;  // +1 enters chunk 0 and ripples through the all-ones chunks
+        const int tz = notO ? __ffs((int)notO) - 1 : 32;
+        if (lane <= tz) chunk_add_word<MC>(r, 1u);
+        rs = sY;
+      }
+    }
+  }
+  const uint32_t NZ = __ballot_sync(FULL, !chunk_is_zero<MC>(r));
+  Result res;
+  int T;
+  if (top) {
+    T = W;
+  } else if (NZ == 0) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) out[k] = 0;
+    res.sgn = 0; res.exp = 0; res.zero = true;
+    res.amb = true;  // a zero short difference says nothing about the exact one
+    return res;
+  } else {
+    const int h = 31 - __clz((int)NZ);
+    const int kk = __shfl_sync(FULL, chunk_top<MC>(r), h);
+    T = h * MC + kk;
+  }
+  {
+    const int last = T - n + 1;
+    bool nz = false, nf = false;
+#pragma unroll
+    for (int k = 0; k < MC; ++k) {
+      const int f = lane * MC + k;
+      if (f >= chk && f < last) {
+        nz |= r[k] != 0u;
+        nf |= r[k] != 0xFFFFFFFFu;
+      }
+    }
+    if (!__any_sync(FULL, nz) || !__any_sync(FULL, nf)) {
+      res.sgn = 0; res.exp = 0; res.zero = false;
+      res.amb = true;
+      return res;
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int k = 0; k < MC; ++k) fr[IX::at(lane * MC + k)] = r[k];
+  if (lane == 0) fr[IX::at(W)] = top;
+  __syncwarp();
+  const int lowest = T - n + 1;  // >= chk + 1 once the test has passed
+#pragma unroll
+  for (int k = 0; k < M; ++k) out[k] = fr[IX::at(lowest + lane * M + k)];
   __syncwarp();
   res.sgn = rs;
   res.exp = base + lowest;
@@ -498,10 +624,12 @@ __device__ __forceinline__ int product_top(const uint32_t (&lo)[M], const uint32
 
 // trunc_n(a - P) where P = (product in sp, 2n limbs, exponent ep, sign sp_sgn)
 // and a = (sa staged n limbs, sign sa_sgn, exponent ea, a_zero).  Chooses the
-// frame placement described at combine().
-template <int M, class IX = IxPlain, class SMEM>
+// frame placement described at combine().  CUT, lc >= 0: sp holds a short
+// product whose difference from the exact one is below the weight of its
+// limb lc (see combine); lc is carried to the frame where P's limbs are used.
+template <int M, class IX = IxPlain, bool CUT = false, class SMEM>
 __device__ __forceinline__ Result sub_product(const SMEM& sm, int sa_sgn, int ea, bool a_zero,
-                                              int sp_sgn, int ep, bool p_zero, uint32_t (&out)[M]) {
+                                              int sp_sgn, int ep, bool p_zero, uint32_t (&out)[M], int lc = -1) {
   constexpr int n = 32 * M;
   const int neg_p = sp_sgn ^ 1;  // a - P = a + (-P)
   if (p_zero) {
@@ -517,28 +645,32 @@ __device__ __forceinline__ Result sub_product(const SMEM& sm, int sa_sgn, int ea
   }
   Staged X, Y;
   int base;
+  int chk = -1;  // frame limb of P's limb lc; P's value is not used in the stand-in case
   if (a_zero) {
     X = Staged{sm.sa, 0, 0};
     Y = Staged{sm.sp, 0, 2 * n};
     base = ep;
+    if (lc >= 0) chk = lc;
   } else {
     const long long delta = (long long)ea - (long long)ep;
     if (delta > 2 * n) {          // P entirely below a by >= 1 limb of a's frame
       X = Staged{sm.sa, 2, n};
       Y = Staged{nullptr, 0, 1};
       base = ea - 2;
-    } else if (delta < -n) {      // a entirely below P
+    } else if (delta < -n) {      // a entirely below P (the stand-in for a is below P's limb 0 too)
       X = Staged{nullptr, 0, 1};
       Y = Staged{sm.sp, 2, 2 * n};
       base = ep - 2;
+      if (lc >= 0) chk = lc + 2;
     } else {
       const int o = delta < 0 ? (int)delta : 0;
       X = Staged{sm.sa, (int)delta - o, n};
       Y = Staged{sm.sp, -o, 2 * n};
       base = ep + o;
+      if (lc >= 0) chk = lc - o;
     }
   }
-  return combine<M, IX>(X, sa_sgn, Y, neg_p, base, sm.sa, out);
+  return combine<M, IX, CUT>(X, sa_sgn, Y, neg_p, base, sm.sa, out, chk);
 }
 
 }  // namespace hk

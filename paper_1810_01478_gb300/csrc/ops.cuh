@@ -65,33 +65,55 @@ struct Ops {
     for (int kt = 0; m - 1 > 128 * kt; ++kt) s += m - 128 * kt;
     return s;
   }
-  // tcgen05.mma instructions of one 128-row item (the same walk as the MMA warp)
-  static double tc_mmas_per_item() {
+  // tcgen05.mma instructions of one 128-row item forming the positions from
+  // q up (the same walk as the MMA warp)
+  static double tc_mmas_per_item(int q) {
     using S = TcShape<M>;
     double c = 0;
-    for (int t = 0; t < S::T; ++t) {
-      const int lo = std::max(0, 256 * t - S::D + 1) >> 6, hi = std::min(S::D - 1, 256 * t + 255) >> 6;
+    for (int t = 0; t < S::tiles(q); ++t) {
+      const int qt = q + 256 * t;
+      const int lo = std::max(0, qt - S::D + 1) >> 6, hi = std::min(S::D - 1, qt + 255) >> 6;
       for (int kb = lo; kb <= hi; ++kb)
         for (int s4 = 0; s4 < 4; ++s4) {
           const int k0 = 64 * kb + 16 * s4;
-          if (!(k0 > 256 * t + 255 || k0 + 15 < 256 * t - S::D + 1)) c += 1;
+          if (!(k0 > qt + 255 || k0 + 15 < qt - S::D + 1)) c += 1;
         }
     }
     return c;
   }
   static int tc_grid(int device) { return std::max(1, sm_count(device) - 1); }
   static size_t tc_p_words(int grid) { return (size_t)grid * 2 * TC_ROWS * TcShape<M>::PL; }
+  // the undecided-row records of up to cap items: count, total, 2 spare,
+  // listed[cap], list[cap], mask[4 cap] (ints; zero when allocated)
+  static size_t tc_redo_ints(size_t cap) { return 4 + 6 * cap; }
+  static TcCut tc_cut(int* redo, size_t cap) {
+    return TcCut{TcShape<M>::QCUT, redo + 4 + cap, redo, redo + 4, reinterpret_cast<uint32_t*>(redo + 4 + 2 * cap),
+                 nullptr};
+  }
 
+  // A short-product launch over the items, then the re-run of the items it
+  // listed with whole products (a fixed grid whose blocks read the count on
+  // the device and leave at once when there is nothing to re-run).
   template <class Items>
-  static cudaError_t tc_launch(const Items& it, int n_items, const uint16_t* DB, int pitch, const uint16_t* DU,
-                               uint32_t* P, int grid, int* err, cudaStream_t s) {
+  static cudaError_t tc_launch(const Items& it, int n_items, int* redo, size_t redo_cap, const uint16_t* DB,
+                               int pitch, const uint16_t* DU, uint32_t* P, int grid, int* err, cudaStream_t s) {
     if constexpr (kTc) {
+      using R = TcRedo<Items>;
       cudaError_t e = cudaFuncSetAttribute(k_tc_fused<M, Items>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)tc_smem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_tc_fused<M, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem);
       if (e != cudaSuccess) return e;
-      const int g = std::min(grid, n_items);
-      if (g <= 0) return cudaSuccess;
-      k_tc_fused<M, Items><<<g, TC_THREADS, tc_smem, s>>>(it, DB, pitch, DU, P, err);
+      if (n_items <= 0 || grid <= 0) return cudaSuccess;
+      if ((size_t)n_items > redo_cap) return cudaErrorInvalidValue;
+      const TcCut cut = tc_cut(redo, redo_cap);
+      if ((e = cudaMemsetAsync(cut.count, 0, sizeof(int), s)) != cudaSuccess) return e;
+      k_tc_fused<M, Items><<<std::min(grid, n_items), TC_THREADS, tc_smem, s>>>(it, cut, DB, pitch, DU, P, err);
+      TcCut whole = cut;
+      whole.q = 0;
+      whole.total = redo + 1;
+      k_tc_fused<M, R><<<grid, TC_THREADS, tc_smem, s>>>(R{it, cut.list, cut.count, cut.listed, cut.mask}, whole, DB,
+                                                         pitch, DU, P, err);
       return cudaGetLastError();
     } else {
       return cudaErrorNotSupported;
@@ -119,18 +141,20 @@ struct Ops {
       using S = TcShape<M>;
       const int cnt = (int)count, pitch = cnt + TC_ROWS, grid = tc_grid(dev);
       const size_t db = (size_t)S::ND * pitch, du = (size_t)S::ND * cnt, pw = tc_p_words(grid);
+      const size_t ri = tc_redo_ints((size_t)cnt);
       uint8_t* buf = nullptr;
-      cudaError_t e = cudaMallocAsync(&buf, (db + du) * 2 + pw * 4 + 16, s);
+      cudaError_t e = cudaMallocAsync(&buf, (db + du) * 2 + pw * 4 + 16 + ri * 4, s);
       if (e != cudaSuccess) return e;
       uint16_t* DB = reinterpret_cast<uint16_t*>(buf);
       uint16_t* DU = DB + db;
       uint32_t* P = reinterpret_cast<uint32_t*>(DU + du);
       int* flag = reinterpret_cast<int*>(P + pw);
+      int* redo = flag + 4;
       cudaMemsetAsync(DB, 0, db * 2, s);
-      cudaMemsetAsync(flag, 0, sizeof(int), s);
+      cudaMemsetAsync(flag, 0, 16 + ri * 4, s);
       tc_digits(x.mant, 0, cnt, 0, DU, 0, 0, dev, s);
       tc_digits(y.mant, 0, cnt, 0, DB, 1, pitch, dev, s);
-      e = tc_launch(TcBatch<M>{a, x, y, out, cnt}, cnt, DB, pitch, DU, P, grid, flag, s);
+      e = tc_launch(TcBatch<M>{a, x, y, out, cnt}, cnt, redo, (size_t)cnt, DB, pitch, DU, P, grid, flag, s);
       int host_flag = 0;
       if (e == cudaSuccess) e = cudaMemcpyAsync(&host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -295,13 +319,21 @@ struct Ops {
         if (r == HK_OK) cap = need;
         return r;
       };
+      int* const redo_before = c.tc_redo;
       if ((st = grow(c.tc_db, c.tc_db_cap, (size_t)S::ND * tc_pitch, 2)) ||
           (st = grow(c.tc_du, c.tc_du_cap, (size_t)S::ND * N, 2)) ||
-          (st = grow(c.tc_p, c.tc_p_cap, tc_p_words(tc_g), 4)))
+          (st = grow(c.tc_p, c.tc_p_cap, tc_p_words(tc_g), 4)) ||
+          (st = grow(c.tc_redo, c.tc_redo_ints, tc_redo_ints((size_t)tc_trail_items(N, 0)), 4)))
         return st;
-      // rows past N stay zero: they fill the last 128-row tile of a column
-      if ((st = check_cuda(c, cudaMemsetAsync(c.tc_db, 0, (size_t)S::ND * tc_pitch * 2, c.stream), "clearing")))
+      // rows past N stay zero: they fill the last 128-row tile of a column;
+      // the undecided-row records start clear (the running total only when
+      // the records are new)
+      const size_t keep = c.tc_redo == redo_before ? 4 : 0;
+      if ((st = check_cuda(c, cudaMemsetAsync(c.tc_db, 0, (size_t)S::ND * tc_pitch * 2, c.stream), "clearing")) ||
+          (st = check_cuda(c, cudaMemsetAsync(c.tc_redo + keep, 0, (c.tc_redo_ints - keep) * 4, c.stream),
+                           "clearing")))
         return st;
+      c.tc_mmas_whole = tc_mmas_per_item(0);
     }
     uint32_t* FU = c.ntt_buf;
     uint32_t* FB = c.ntt_buf ? c.ntt_buf + per * (size_t)N : nullptr;
@@ -400,11 +432,13 @@ struct Ops {
         const bool tc_step = tc && rows >= HK_TC_MIN_ROWS;
         if (tc_step) {
           const int items = tc_trail_items(N, i);
-          const cudaError_t e = tc_launch(TcTrail<M>{c.A.view(), c.U.view(), N, i}, items, c.tc_db, tc_pitch,
-                                          c.tc_du, c.tc_p, tc_g, c.d_err, s);
+          const size_t cap = (c.tc_redo_ints - 4) / 6;
+          const cudaError_t e = tc_launch(TcTrail<M>{c.A.view(), c.U.view(), N, i}, items, c.tc_redo, cap, c.tc_db,
+                                          tc_pitch, c.tc_du, c.tc_p, tc_g, c.d_err, s);
           if ((st = check_cuda(c, e, "launching the tensor-core update")) != HK_OK) return st;
+          count_launch(c);  // the re-run launch
           if (c.prof) {
-            c.tc_mmas += items * tc_mmas_per_item();
+            c.tc_mmas += items * tc_mmas_per_item(TcShape<M>::QCUT);
             c.tc_ev.push_back({e1, prof_mark(c)});
           }
         } else {

@@ -24,6 +24,20 @@
 // both 128.  The stored cores of U_c (about 66 KB at 768 limbs) serve every
 // tile and K-step of the column.
 //
+// Short products.  The result keeps n limbs below its leading one, so the
+// product's low positions matter only through the carry they send up.  A
+// launch forms the positions from Q up (Q = QCUT, a multiple of 32, about
+// D - 16 limbs' worth of positions below the middle): the omitted terms
+// sum to less than 2^(7Q + 18) in absolute value (below 2^24 at each
+// position, as above, and the positions' weights 2^(7q) form a geometric
+// series of ratio 2^-7), and combine() takes the truncation
+// of the formed difference only where that bound cannot change it (a limb
+// between the bound and the result's last limb that is neither 0 nor all
+// ones).  Rows it cannot decide are not written; their items go on a list
+// that a second launch of the same kernel re-runs with Q = 0 (the whole
+// product), forming only those rows.  Every result is therefore the
+// truncation of the exact a - x y, as on every other product path.
+//
 // Schedule.  Tiles t (256 positions each) run in staggered pairs on two
 // 256-column fp32 accumulators: the pair's K-blocks (64 digits, one bulk-copy
 // stage) are loaded once and used by both tiles where their bands overlap,
@@ -64,10 +78,19 @@ struct TcShape {
   static constexpr int Z0 = 320;                              // staging: digit y of U at su[y + Z0]
   static constexpr int ZN = (Z0 - XMIN + 1 + 7) / 8 * 8;
   static constexpr int PD = ((D + 31) / 32 + 7) / 8 * 8;      // digits per lane of the recode
+  // first position of a short product: its limb 7 QCUT / 32 lies GUARD + 2
+  // limbs below the middle limb n of the 2n-limb product (the guard absorbs
+  // cancellation in a - x y and leaves room for the determinacy test)
+  static constexpr int GUARD = 16;
+  static constexpr int QCUT = 32 * ((n - GUARD - 2) / 7);
+  static constexpr int tiles(int q) { return (2 * D - 1 - q + 255) / 256; }
   static_assert((long long)D * 4096 < (1ll << 24), "digit sums must stay exact in fp32");
   static_assert(2 * n <= PL, "emitted limbs must cover the product");
   static_assert(32 * PD >= ND, "recode lanes must cover every digit slot");
   static_assert(Z0 - XMAX - 14 >= 0, "staging must cover the lowest Hankel index");
+  static_assert(QCUT > 0 && 7 * QCUT / 32 + 2 + GUARD <= n, "the cut must leave the guard below the middle");
+  static_assert(7 * QCUT + 18 <= 32 * n, "a short product stays below 2^(64 n)");
+  static_assert(tiles(QCUT) <= T, "a short product's limbs fit the row");
 };
 
 #include "../../include/hk.h"  // HK_TC_MIN_ROWS
@@ -217,15 +240,15 @@ __device__ __forceinline__ uint64_t tc_sdesc(uint32_t saddr, uint32_t lbo, uint3
          ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
 }
 
-// K-blocks (64 digits) of tile t: [lo, hi]
+// K-blocks (64 digits) of the tile of positions [qt, qt + 256): [lo, hi]
 template <int M>
-__device__ __forceinline__ void tc_band(int t, int& lo, int& hi) {
+__device__ __forceinline__ void tc_band(int qt, int& lo, int& hi) {
   constexpr int D = TcShape<M>::D;
-  lo = max(0, 256 * t - D + 1) >> 6;
-  hi = min(D - 1, 256 * t + 255) >> 6;
+  lo = max(0, qt - D + 1) >> 6;
+  hi = min(D - 1, qt + 255) >> 6;
 }
 
-// The MMAs of K-block kb (ring stage s) for tile t into the accumulator at
+// The MMAs of K-block kb (ring stage s) for the tile at qt into the accumulator at
 // column d_tmem: the 16-digit sub-blocks that meet the tile's band.  first:
 // no MMA of the tile issued yet (the first one overwrites the accumulator).
 // Returns the new `first`.
@@ -239,9 +262,9 @@ __device__ __forceinline__ void tc_band(int t, int& lo, int& hi) {
 // keeps the single issuing thread to a few instructions per MMA.
 template <int M>
 __device__ __forceinline__ bool tc_issue_kblock(uint32_t d_tmem, uint64_t adesc0, uint64_t bdesc0, int s, int kb,
-                                                int t, bool first) {
+                                                int qt, bool first) {
   using S = TcShape<M>;
-  const int q_lo = 256 * t - S::D + 1, q_hi = 256 * t + 255;  // the tile's digit band
+  const int q_lo = qt - S::D + 1, q_hi = qt + 255;  // the tile's digit band
   const uint64_t ad = adesc0 + (uint64_t)(1024 * s);
   const int k00 = 64 * kb;
   const uint64_t bd = bdesc0 + (uint64_t)(int64_t)(k00 - q_hi - S::XMIN);
@@ -325,6 +348,11 @@ __global__ void k_tc_digits(const uint32_t* __restrict__ mant, int64_t first, in
   }
 }
 
+// The warp's lanes bring `words` words at p into L2 (one 128-byte line each).
+__device__ __forceinline__ void prefetch_l2(const uint32_t* p, int words) {
+  for (int l = lane_id(); 32 * l < words; l += 32) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + 32 * l));
+}
+
 // ---------------------------------------------------------------------------
 // work items: one U column and up to 128 consecutive rows of digit matrix B
 // ---------------------------------------------------------------------------
@@ -368,6 +396,7 @@ struct TcTrail {
     row0 = i + 1 + r0;
     nrows = min(128, m() - r0);
   }
+  __device__ const uint32_t* addend(int ucol, int r) const { return A.mant + tri_pos(N, r, ucol) * (32 * M); }
   __device__ void operands(int ucol, int r, TcFused& f) const {
     constexpr int n = 32 * M;
     const int c = ucol;
@@ -384,6 +413,8 @@ struct TcTrail {
     f.out = A;
     f.opos = apos;
   }
+  static constexpr bool kRedo = false;
+  __device__ uint32_t take_rows(int, int) const { return 0xFFFFFFFFu; }
 };
 
 // Elementwise out[e] = trunc(a[e] - x[e] y[e]): item e is U row e with the single digit row e.
@@ -397,6 +428,7 @@ struct TcBatch {
     row0 = idx;
     nrows = 1;
   }
+  __device__ const uint32_t* addend(int, int r) const { return a.mant + (int64_t)r * (32 * M); }
   __device__ void operands(int ucol, int r, TcFused& f) const {
     constexpr int n = 32 * M;
     const int64_t e = r;
@@ -411,6 +443,47 @@ struct TcBatch {
     f.yz = y.mant[e * n + n - 1] == 0u;
     f.out = out;
     f.opos = e;
+  }
+  static constexpr bool kRedo = false;
+  __device__ uint32_t take_rows(int, int) const { return 0xFFFFFFFFu; }
+};
+
+// Where a launch's short products start, and where it lists the rows it
+// could not decide (q > 0 only).
+struct TcCut {
+  int q;            // first product position formed: a multiple of 32, 0 for the whole product
+  int* list;        // items with undecided rows
+  int* count;       // entries of list (zero before the launch)
+  int* listed;      // per item: 1 once it is in list
+  uint32_t* mask;   // per item, 4 words: undecided rows (bit j of word w: row 32 w + j)
+  int* total;       // re-run launch: running count of the items it re-ran (profiling)
+};
+
+// The re-run of the listed items with whole products: only the rows in the
+// item's mask are formed (the others were written by the first launch, in
+// place).  Reading a mask resets it, and the listed flag, for the next step.
+template <class Base>
+struct TcRedo {
+  Base base;
+  const int* list;
+  const int* count;
+  int* listed;
+  uint32_t* mask;
+  static constexpr bool kRedo = true;
+  __device__ int items() const { return *count; }
+  __device__ void item(int idx, int& ucol, int& row0, int& nrows) const { base.item(list[idx], ucol, row0, nrows); }
+  __device__ const uint32_t* addend(int ucol, int r) const { return base.addend(ucol, r); }
+  __device__ void operands(int ucol, int r, TcFused& f) const { base.operands(ucol, r, f); }
+  // rows of warp q (its 32 TMEM lanes) to form; called once by the whole warp
+  __device__ uint32_t take_rows(int idx, int q) const {
+    const int id = list[idx];
+    const uint32_t m = *reinterpret_cast<volatile uint32_t*>(mask + (size_t)id * 4 + q);
+    __syncwarp();
+    if (lane_id() == 0) {
+      mask[(size_t)id * 4 + q] = 0u;
+      if (q == 0) listed[id] = 0;
+    }
+    return m;
   }
 };
 
@@ -449,16 +522,22 @@ struct TcSmem {
 // ---------------------------------------------------------------------------
 // DB: kgroup-major digit matrix, `pitch` rows per kgroup (rows beyond the
 // valid ones are zero); DU: U digits, ND per row; P: per block 2 x 128 rows x
-// PL limbs of products.
+// PL limbs of products (a row holds the product's limbs from 7 q / 32 up).
 template <int M, class Items>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_tc_fused(Items items, const uint16_t* __restrict__ DB, int pitch, const uint16_t* __restrict__ DU,
+    k_tc_fused(Items items, TcCut cut, const uint16_t* __restrict__ DB, int pitch, const uint16_t* __restrict__ DU,
                uint32_t* __restrict__ P, int* err) {
   using S = TcShape<M>;
   using SM = TcSmem<M>;
   constexpr int n = S::n;
   extern __shared__ __align__(1024) uint8_t tc_smem[];
   if (*err & (ERR_NOT_PD | ERR_TIMEOUT)) return;
+  const int n_items = items.items();
+  if (cut.total && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(cut.total, n_items);
+  if ((int)blockIdx.x >= n_items) return;  // the re-run launch has a fixed grid
+  const int Q = cut.q;                     // tiles start at positions Q + 256 t
+  const int TT = S::tiles(Q);
+  const int L0 = 7 * Q / 32;               // first limb formed
   const int warp = threadIdx.x >> 5, lane = lane_id();
   uint8_t* hc = tc_smem + SM::hc;
   uint16_t* su = reinterpret_cast<uint16_t*>(tc_smem + SM::su);
@@ -500,7 +579,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int n_items = items.items();
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -532,10 +610,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(hc_full);
       // A-operand stages of every tile pair
-      for (int j = 0; 2 * j < S::T && ok; ++j) {
+      for (int j = 0; 2 * j < TT && ok; ++j) {
         int lo_a, hi_a, lo_b = 1, hi_b = 0;
-        tc_band<M>(2 * j, lo_a, hi_a);
-        if (2 * j + 1 < S::T) tc_band<M>(2 * j + 1, lo_b, hi_b);
+        tc_band<M>(Q + 512 * j, lo_a, hi_a);
+        if (2 * j + 1 < TT) tc_band<M>(Q + 512 * j + 256, lo_b, hi_b);
         const int hi = max(hi_a, hi_b);
         for (int kb = lo_a; kb <= hi; ++kb, ++L) {
           const int s = L % TC_STAGES;
@@ -569,10 +647,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
         if (!mbar_wait(hc_full, k & 1, abort, 3)) break;
         tc_fence_after();
-        for (int j = 0; 2 * j < S::T && ok; ++j) {
+        for (int j = 0; 2 * j < TT && ok; ++j) {
           int lo0, hi0, lo1 = 1, hi1 = 0;
-          tc_band<M>(2 * j, lo0, hi0);
-          if (2 * j + 1 < S::T) tc_band<M>(2 * j + 1, lo1, hi1);
+          tc_band<M>(Q + 512 * j, lo0, hi0);
+          if (2 * j + 1 < TT) tc_band<M>(Q + 512 * j + 256, lo1, hi1);
           bool f0 = true, f1 = true;
           const int hi_all = max(hi0, hi1);
           for (int kb = lo0; kb <= hi_all; ++kb) {
@@ -589,7 +667,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
               }
-              f0 = tc_issue_kblock<M>(tmem, adesc0, bdesc0, s, kb, 2 * j, f0);
+              f0 = tc_issue_kblock<M>(tmem, adesc0, bdesc0, s, kb, Q + 512 * j, f0);
               if (kb == hi0) {
                 tc_commit(acc_full);
                 ++u0;
@@ -603,7 +681,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 tc_fence_after();
               }
-              f1 = tc_issue_kblock<M>(tmem + 256u, adesc0, bdesc0, s, kb, 2 * j + 1, f1);
+              f1 = tc_issue_kblock<M>(tmem + 256u, adesc0, bdesc0, s, kb, Q + 512 * j + 256, f1);
               if (kb == hi1) {
                 tc_commit(acc_full + 1);
                 ++u1;
@@ -627,7 +705,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int set = (warp - 2) >> 2;  // items k = set (mod 2)
     const int q = warp & 3;           // this warp's TMEM lanes 32q .. 32q + 31
     const int mrow = 32 * q + lane;
-    constexpr int C0 = (S::T + 1) / 2, C1 = S::T / 2;  // tiles per item in accumulators 0 and 1
+    const int C0 = (TT + 1) / 2, C1 = TT / 2;  // tiles per item in accumulators 0 and 1
     uint32_t* nb = reinterpret_cast<uint32_t*>(tc_smem + SM::comb) + (size_t)(warp - 2) * SM::comb_words;
     uint32_t* pset = P + (size_t)(blockIdx.x * 2 + set) * TC_ROWS * S::PL;
     bool ok = true;
@@ -643,7 +721,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int u0 = k * C0, u1 = k * C1;  // uses of accumulators 0 and 1 before this item
       uint32_t* prow = pset + (size_t)mrow * S::PL;
       long long acc = 0;  // signed carry into the next limb
-      for (int t = 0; t < S::T; ++t) {
+      for (int t = 0; t < TT; ++t) {
         const int b = t & 1;
         if (!mbar_wait(acc_full + b, (b ? u1 : u0) & 1, abort, 8 + b)) {
           ok = false;
@@ -654,8 +732,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // Two independent chains: the tile's low half (groups 0..3, limbs
         // 0..27, starting from the carry of the previous tile) and its high
         // half (groups 4..7, limbs 28..55, from zero); the low half's carry
-        // is then added into the high half.  Positions 256t + 32g + u are
-        // columns 255 - 32g - u.
+        // is then added into the high half.  Positions Q + 256t + 32g + u
+        // are columns 255 - 32g - u; the tile's limbs are L0 + 56t + w.
         long long acc_hi = 0;
         const uint32_t tcol = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * 256);
 #pragma unroll
@@ -680,11 +758,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
         for (int w = 0; w < 14; ++w)
           reinterpret_cast<uint4*>(prow + 56 * t)[w] = make_uint4(lim[4 * w], lim[4 * w + 1], lim[4 * w + 2], lim[4 * w + 3]);
-        // the product is below 2^(64 n): the limbs past 2n and the last carry are zero
-        uint32_t stray = (t == S::T - 1) ? (uint32_t)(acc != 0) : 0u;
+        // the product (short or whole) is in [0, 2^(64 n)): the limbs past
+        // 2n and the last carry are zero
+        uint32_t stray = (t == TT - 1) ? (uint32_t)(acc != 0) : 0u;
 #pragma unroll
         for (int w = 0; w < 56; ++w)
-          if (56 * t + w >= 2 * n) stray |= lim[w];
+          if (L0 + 56 * t + w >= 2 * n) stray |= lim[w];
         if (stray) atomicOr(err, ERR_LOOP);
       }
       if (!ok) break;
@@ -693,8 +772,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       // trunc(a - P) for this warp's rows, one row at a time with the whole warp
       int ucol, row0, nrows;
       items.item(it, ucol, row0, nrows);
+      const uint32_t rows = items.take_rows(it, q);
+      const int lc = Q > 0 ? L0 + 2 : -1;  // the omitted terms are below 2^(7Q + 18) < 2^(32 (L0 + 1))
+      uint32_t undecided = 0;
+      // the next row's addend and product limbs are brought into L2 while
+      // this one is formed: one row's loads are otherwise all latency
+      if (rows & 1u) {
+        prefetch_l2(items.addend(ucol, row0 + 32 * q), n);
+        prefetch_l2(pset + (size_t)(32 * q) * S::PL, 2 * n - L0);
+      }
       for (int j = 0; j < 32 && 32 * q + j < nrows; ++j) {
+        if (!((rows >> j) & 1u)) continue;
         const int mm = 32 * q + j;
+        if (j + 1 < 32 && 32 * q + j + 1 < nrows && ((rows >> (j + 1)) & 1u)) {
+          prefetch_l2(items.addend(ucol, row0 + mm + 1), n);
+          prefetch_l2(pset + (size_t)(mm + 1) * S::PL, 2 * n - L0);
+        }
         TcFused f;
         items.operands(ucol, row0 + mm, f);
         const uint32_t* pr = pset + (size_t)mm * S::PL;
@@ -705,7 +798,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         load_chunk<M>(f.amant, av);
         if (!p_zero) {
 #pragma unroll
-          for (int w = 0; w < 2 * M; ++w) pv[w] = __ldcg(pr + 32 * w + lane);
+          for (int w = 0; w < 2 * M; ++w) {
+            const int l = 32 * w + lane - L0;  // limbs below L0 are zero in a short product
+            pv[w] = l >= 0 ? __ldcg(pr + l) : 0u;
+          }
 #pragma unroll
           for (int w = 0; w < 2 * M; ++w) sm.sp[IxPad::at(32 * w + lane)] = pv[w];
         }
@@ -714,9 +810,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
         const bool a_zero = sm.sa[IxPad::at(n - 1)] == 0u;
         uint32_t o[M];
-        const Result res = sub_product<M, IxPad>(sm, f.asgn, f.aexp, a_zero, f.sx ^ f.sy, f.ex + f.ey, p_zero, o);
-        store_result<M>(f.out, f.opos, res, o);
+        // Usually a's leading limb lies within a few limbs of the product's,
+        // and the short difference fits a frame of n + 32 limbs from the
+        // product's limb L0: frame limb 0 = limb L0, a at frame limb
+        // ea - ep - L0 in [0, 32]; the omitted terms are below frame limb 1.
+        const long long da = (long long)f.aexp - (long long)(f.ex + f.ey) - L0;
+        Result res;
+        if (lc >= 0 && !a_zero && !p_zero && da >= 0 && da <= 32)
+          res = combine_narrow<M + 1, M, IxPad>(Staged{sm.sa, (int)da, n}, f.asgn, Staged{sm.sp, -L0, 2 * n},
+                                                f.sx ^ f.sy ^ 1, f.ex + f.ey + L0, sm.sa, o, 2);
+        else
+          res = sub_product<M, IxPad, true>(sm, f.asgn, f.aexp, a_zero, f.sx ^ f.sy, f.ex + f.ey, p_zero, o, lc);
+        if (res.amb) undecided |= 1u << j;
+        else store_result<M>(f.out, f.opos, res, o);
         __syncwarp();
+      }
+      if (undecided && lane == 0) {
+        cut.mask[(size_t)it * 4 + q] = undecided;
+        if (atomicExch(cut.listed + it, 1) == 0) cut.list[atomicAdd(cut.count, 1)] = it;
       }
     }
   }

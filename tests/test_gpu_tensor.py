@@ -69,6 +69,49 @@ def test_tensor_factor_matches_ntt(N, bits):
     assert digests[0] == digests[1]
 
 
+@pytest.mark.parametrize("b,N,bits,rerun", [(1, 300, 8192, "most"), (2, 320, 12288, "few")])
+def test_short_products_and_their_reruns(b, N, bits, rerun):
+    """The trailing update forms only the product positions that can reach
+    the truncated result and re-runs, with whole products, the 128-row items
+    where that cannot be decided.  beta = 1 at 8192 bits keeps every entry
+    an exact integer (mu_j = j!, D_i = (i!)^2), so the guard limbs of the
+    differences are zero and nearly every item is re-run; at beta = 1/2 the
+    entries stop being integers after the first step (L[r][1] is already a
+    proper fraction) and only that step's items are re-run.  Both factors
+    must equal the NTT path's bit for bit."""
+    import paper_1810_01478_gb300 as hk
+    from tests.digest import factor_digest
+    hk.load()
+    digests, prof = [], None
+    try:
+        for alg in (hk.HK_PRODUCT_NTT, hk.HK_PRODUCT_TENSOR):
+            hk.hk_set_product_algorithm(alg)
+            with hk.Hankel(0) as h:
+                h.moments(1, b, N, bits)
+                hk.hk_set_profiling(h.ctx, True)
+                h.ldlt()
+                prof = hk.hk_get_profile(h.ctx)
+                digests.append(factor_digest(h, hk, N))
+    finally:
+        hk.hk_set_product_algorithm(hk.HK_PRODUCT_AUTO)
+    assert digests[0] == digests[1]
+    items = sum(hk_items(N, i) for i in range(N - 1) if N - 1 - i >= hk.HK_TC_MIN_ROWS)
+    assert prof["tc_launches"] > 0
+    if rerun == "most":
+        assert prof["tc_redo_items"] > 0.5 * items, (prof["tc_redo_items"], items)
+    else:
+        assert prof["tc_redo_items"] < 0.05 * items, (prof["tc_redo_items"], items)
+
+
+def hk_items(N, i):
+    """128-row items of step i of the tensor-core trailing update."""
+    m, s, kt = N - 1 - i, 0, 0
+    while m - 1 > 128 * kt:
+        s += m - 128 * kt
+        kt += 1
+    return s
+
+
 def test_tensor_full_factor_golden():
     """beta = 1/2, N = 1024, 8192 bits: the whole factor and X against the
     oracle's digests (tests/golden/c5_1024_8192.json), tensor-core updates in
