@@ -810,17 +810,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         __syncwarp();
         const bool a_zero = sm.sa[IxPad::at(n - 1)] == 0u;
         uint32_t o[M];
-        // Usually a's leading limb lies within a few limbs of the product's,
-        // and the short difference fits a frame of n + 32 limbs from the
-        // product's limb L0: frame limb 0 = limb L0, a at frame limb
-        // ea - ep - L0 in [0, 32]; the omitted terms are below frame limb 1.
-        const long long da = (long long)f.aexp - (long long)(f.ex + f.ey) - L0;
+        // A short product's difference on a frame of n + 32 limbs whose top
+        // is just above the higher of the two leading limbs: frame limb 0 is
+        // the product's limb F0 = max(n - 32, d - 32), d = ea - ep (the
+        // addend's limb 0 in the product's limbs).  Limbs of either operand
+        // below F0 are left out like the omitted terms: all three together
+        // are below 2^(32 F0 + 1) + 2^(32 L0 + 18), under frame limb
+        // max(L0 - F0, 0) + 2.  A product wholly below the addend (d > 2n)
+        // goes through the exact stand-in of sub_product instead.
+        const long long d = (long long)f.aexp - (long long)(f.ex + f.ey);
         Result res;
-        if (lc >= 0 && !a_zero && !p_zero && da >= 0 && da <= 32)
-          res = combine_narrow<M + 1, M, IxPad>(Staged{sm.sa, (int)da, n}, f.asgn, Staged{sm.sp, -L0, 2 * n},
-                                                f.sx ^ f.sy ^ 1, f.ex + f.ey + L0, sm.sa, o, 2);
-        else
+        if (lc >= 0 && !p_zero && d <= 2 * n) {
+          const int F0 = (int)max((long long)n - 32, (a_zero ? (long long)n : d) - 32);
+          const bool a_out = a_zero || d - F0 < -(long long)n;  // the addend wholly below the frame
+          res = combine_narrow<M + 1, M, IxPad>(Staged{sm.sa, a_out ? 0 : (int)(d - F0), a_out ? 0 : n}, f.asgn,
+                                                Staged{sm.sp, -F0, 2 * n}, f.sx ^ f.sy ^ 1, f.ex + f.ey + F0, sm.sa,
+                                                o, max(L0 - F0, 0) + 2);
+        } else {
           res = sub_product<M, IxPad, true>(sm, f.asgn, f.aexp, a_zero, f.sx ^ f.sy, f.ex + f.ey, p_zero, o, lc);
+        }
         if (res.amb) undecided |= 1u << j;
         else store_result<M>(f.out, f.opos, res, o);
         __syncwarp();
