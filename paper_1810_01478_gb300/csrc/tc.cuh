@@ -44,8 +44,9 @@
 // and one accumulator is drained (tcgen05.ld) while the other finishes.
 //
 // Warp roles of the persistent kernel (320 threads, one CTA per SM):
-//   warp 0      producer: builds the Hankel cores of the item's U_c, then
-//               streams the A-operand stages with cp.async.bulk
+//   warp 0      producer: streams the A-operand stages with cp.async.bulk
+//               and builds the Hankel cores of each item's U_c from its
+//               digits (brought in by a bulk copy during the item before)
 //   warp 1      tensor-memory owner and MMA issuer (one thread)
 //   warps 2..9  two sets of four that take the block's items in turn; a
 //               warp drains its 32 TMEM lanes (one row per thread:
@@ -76,7 +77,7 @@ struct TcShape {
   static constexpr int XMAX = 304;
   static constexpr int NHC = (XMAX - XMIN) / 8 + 1;           // stored cores
   static constexpr int Z0 = 320;                              // staging: digit y of U at su[y + Z0]
-  static constexpr int ZN = (Z0 - XMIN + 1 + 7) / 8 * 8;
+  static constexpr int ZN = (Z0 - XMIN + 1 + 7) / 8 * 8 + 8;  // (8 more: the core build reads whole words)
   static constexpr int PD = ((D + 31) / 32 + 7) / 8 * 8;      // digits per lane of the recode
   // first position of a short product: its limb 7 QCUT / 32 lies GUARD + 2
   // limbs below the middle limb n of the 2n-limb product (the guard absorbs
@@ -547,7 +548,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* empty = bar + TC_STAGES;           // [TC_STAGES] stage consumed by its MMAs
   uint64_t* acc_full = bar + 2 * TC_STAGES;    // [2] accumulator holds a finished tile
   uint64_t* acc_empty = acc_full + 2;          // [2] accumulator drained
-  uint64_t* hc_full = acc_empty + 2;           // [1] Hankel cores of the item built ([0] used)
+  uint64_t* hc_full = acc_empty + 2;           // Hankel cores of the item built
+  uint64_t* su_full = hc_full + 1;             // the next item's U digits copied into su
   uint64_t* hc_empty = hc_full + 2;            // [1] MMAs of the item done ([0] used)
   uint64_t* turn = hc_empty + 2;               // [2] set s has drained every tile of its item (turn[s])
   uint64_t* fin = turn + 2;                    // every MMA of the kernel done
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     mbar_init(hc_full, 1);
     mbar_init(hc_empty, 1);
+    mbar_init(su_full, 1);
     mbar_init(turn, 4);
     mbar_init(turn + 1, 4);
     mbar_init(fin, 1);
@@ -582,40 +585,76 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
+    // Per item: the A-operand stages in the pairs' order, the first
+    // TC_STAGES of them issued before the item's Hankel cores are built (the
+    // ring is free once the previous item's MMAs have consumed it), and the
+    // next item's U digits brought into su by a bulk copy as soon as the
+    // cores are built, so that neither the copies nor the staging wait on
+    // the build.
     int L = 0;  // stages issued
     int k = 0;
+    int su_uses = 0;        // bulk copies into su waited for
+    bool su_pending = false;
     bool ok = true;
-    for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
+    // su outside [Z0, Z0 + ND) stays zero: the digits of U past its ends
+    for (int z = lane * 8; z < S::ZN; z += 256)
+      if (z < S::Z0 || z >= S::Z0 + S::ND) *reinterpret_cast<uint4*>(su + z) = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    auto copy_u = [&](int item) {
       int ucol, row0, nrows;
-      items.item(it, ucol, row0, nrows);
-      if (k > 0 && !mbar_wait(hc_empty, (k - 1) & 1, abort, 1)) break;
-      // stage U's digits (zeros outside [0, ND)), then the Hankel cores
-      const uint16_t* du = DU + (int64_t)ucol * S::ND;
-      for (int z = lane * 8; z < S::ZN; z += 256) {
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (z >= S::Z0 && z - S::Z0 < S::ND) v = *reinterpret_cast<const uint4*>(du + (z - S::Z0));
-        *reinterpret_cast<uint4*>(su + z) = v;
+      items.item(item, ucol, row0, nrows);
+      if (lane == 0) {
+        mbar_expect_tx(su_full, S::ND * 2);
+        bulk_g2s(su + S::Z0, DU + (int64_t)ucol * S::ND, S::ND * 2, su_full);
       }
-      __syncwarp();
+      su_pending = true;
+    };
+    // the cores of item k (x = XMIN + 8h, row i of core h = U(-x - i - j), j < 8),
+    // then the copy of the next item's digits
+    auto build = [&](int it) -> bool {
+      if (k > 0 && !mbar_wait(hc_empty, (k - 1) & 1, abort, 1)) return false;
+      if (!mbar_wait(su_full, su_uses & 1, abort, 10)) return false;
+      ++su_uses;
+      su_pending = false;
+      const uint32_t* su32 = reinterpret_cast<const uint32_t*>(su);
+#pragma unroll 4
       for (int row = lane; row < S::NHC * 8; row += 32) {
-        const int h = row >> 3, i = row & 7;
-        const int base = S::Z0 - (S::XMIN + 8 * h) - i;  // su index of U(-x - i - j) at j = 0
-        uint32_t w[4];
-#pragma unroll
-        for (int j = 0; j < 8; j += 2)
-          w[j >> 1] = (uint32_t)su[base - j] | ((uint32_t)su[base - j - 1] << 16);
-        *reinterpret_cast<uint4*>(hc + (size_t)h * 128 + i * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        // the row is su[p + 7], su[p + 6], ..., su[p] with p = Z0 - XMIN - row - 7:
+        // five aligned words from p rounded down, and a byte permutation
+        // that takes the right halves in reverse order
+        const int p = S::Z0 - S::XMIN - row - 7;
+        const uint32_t* v = su32 + (p >> 1);
+        const uint32_t v0 = v[0], v1 = v[1], v2 = v[2], v3 = v[3], v4 = v[4];
+        const uint32_t sel = (p & 1) ? 0x3254u : 0x1032u;
+        *reinterpret_cast<uint4*>(hc + (size_t)row * 16) =
+            make_uint4(__byte_perm(v3, v4, sel), __byte_perm(v2, v3, sel), __byte_perm(v1, v2, sel),
+                       __byte_perm(v0, v1, sel));
       }
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(hc_full);
-      // A-operand stages of every tile pair
+      if (it + (int)gridDim.x < n_items) copy_u(it + gridDim.x);
+      return true;
+    };
+    if (ok) copy_u(blockIdx.x);
+    for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++k) {
+      int ucol, row0, nrows;
+      items.item(it, ucol, row0, nrows);
+      int issued = 0;
+      bool built = false;
       for (int j = 0; 2 * j < TT && ok; ++j) {
         int lo_a, hi_a, lo_b = 1, hi_b = 0;
         tc_band<M>(Q + 512 * j, lo_a, hi_a);
         if (2 * j + 1 < TT) tc_band<M>(Q + 512 * j + 256, lo_b, hi_b);
         const int hi = max(hi_a, hi_b);
-        for (int kb = lo_a; kb <= hi; ++kb, ++L) {
+        for (int kb = lo_a; kb <= hi; ++kb, ++L, ++issued) {
+          if (issued == TC_STAGES && !built) {
+            if (!build(it)) {
+              ok = false;
+              break;
+            }
+            built = true;
+          }
           const int s = L % TC_STAGES;
           if (!mbar_wait(empty + s, ((L / TC_STAGES) & 1) ^ 1, abort, 2)) {
             ok = false;
@@ -631,8 +670,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           __syncwarp();
         }
       }
+      if (ok && !built && !build(it)) ok = false;
     }
-    // stages whose MMAs may not have consumed them: wait for their copies before leaving
+    // copies that may still be in flight: wait for them before leaving
+    if (su_pending) mbar_wait(su_full, su_uses & 1, nullptr);
     if (*abort) {
       for (int q = max(0, L - TC_STAGES); q < L; ++q) mbar_wait(full + q % TC_STAGES, (q / TC_STAGES) & 1, nullptr);
     }
