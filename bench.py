@@ -317,6 +317,18 @@ def tc_digits(n):
     return (32 * n) // 7 + 2
 
 
+def tc_cut(n):
+    """First product position the tensor-core launches form (a multiple of 32
+    about 16 limbs below the middle of the 2n-limb product)."""
+    return 32 * ((n - 16 - 2) // 7)
+
+
+def tc_pairs(D, q):
+    """Digit products k1 + k2 >= q of a D-digit by D-digit convolution: the
+    multiply-adds of a short product that starts at position q."""
+    return sum(min(s, 2 * D - 2 - s) + 1 for s in range(q, 2 * D - 1))
+
+
 def tc_updates(N, min_rows):
     """Fused updates of the tensor-core launches of one LDL^T: every step whose
     trailing triangle has at least min_rows rows, less its look-ahead entry."""
@@ -330,15 +342,18 @@ def tc_updates(N, min_rows):
 
 def tensor_roofline(prof, N, n, min_rows, traffic_per_update, solves):
     """The roofline object of the tensor-core trailing update: algorithmic
-    bf16 flops (2 D^2 per fused update, D balanced 7-bit digits per number:
-    the digit convolution each product is) per second of its launches'
-    device time, against the measured cuBLAS bf16 throughput sustained over a
-    long run (the launches run inside a six-second step)."""
+    bf16 flops per second of its launches' device time, against the measured
+    cuBLAS bf16 throughput sustained over a long run (the launches run inside
+    a multi-second step).  The algorithmic work of a fused update is its short
+    product: 2 flops for every digit product k1 + k2 >= q (D balanced 7-bit
+    digits per number, q = tc_cut(n)); the re-runs with whole products of the
+    rows a short product cannot decide count as executed work only."""
     launches = max(prof["tc_launches"], 1)
     sec = prof["tc_ms"] / 1e3
-    D = tc_digits(n)
+    D, q = tc_digits(n), tc_cut(n)
+    pairs = tc_pairs(D, q)
     upd = tc_updates(N, min_rows) * solves  # the profile covers `solves` factorisations
-    alg = 2.0 * D * D * upd
+    alg = 2.0 * pairs * upd
     executed = prof["tc_mmas"] * 2.0 * 128 * 256 * 16
     pk = measured_peaks()
     if pk and pk.get("bf16_tflops_sustained"):
@@ -350,7 +365,9 @@ def tensor_roofline(prof, N, n, min_rows, traffic_per_update, solves):
                 traffic=traffic_per_update * upd / launches if traffic_per_update is not None else None,
                 kernel="k_tc_fused (Algorithm 1 trailing update, bf16 tcgen05 digit-convolution GEMMs)",
                 peak_note=src,
-                work_per_update=f"2 D^2 = {2 * D * D} flops (D = {D} balanced 7-bit digits per number)",
+                work_per_update=f"{2 * pairs} flops: 2 per digit product at positions >= {q} "
+                                f"(D = {D} balanced 7-bit digits per number; the whole product is {2 * D * D})",
+                rerun_items=int(prof.get("tc_redo_items", 0)),
                 updates=upd, launches=int(prof["tc_launches"]),
                 executed_tflops=executed / sec / 1e12, executed_frac=executed / sec / 1e12 / peak,
                 executed_note="tcgen05.mma instructions issued (128 x 256 x 16 each, including the padding of "

@@ -101,7 +101,8 @@ def test_trailing_roofline_arithmetic():
 
 
 def test_tensor_roofline_arithmetic():
-    """bench.tensor_roofline: algorithmic flops 2 D^2 per fused update of the
+    """bench.tensor_roofline: algorithmic flops of the short products (2 per
+    digit product at positions >= the cut) per fused update of the
     tensor-core launches (every step with at least min_rows trailing rows,
     less its look-ahead entry), times the factorisations profiled, over their
     device time, against the sustained bf16 peak; the executed rate counts
@@ -111,10 +112,15 @@ def test_tensor_roofline_arithmetic():
     upd = sum((N - 1 - i) * (N - i) // 2 - 1 for i in range(N - 1) if N - 1 - i >= min_rows)
     assert bench.tc_updates(N, min_rows) == upd
     D = bench.tc_digits(n)
-    assert D == 3512
+    assert D == 3512 and bench.tc_cut(n) == 3424
+    # the digit products of a D x D convolution at positions >= q, counted directly
+    for d, q in ((5, 0), (5, 3), (7, 6), (9, 16)):
+        assert bench.tc_pairs(d, q) == sum(1 for a in range(d) for b in range(d) if a + b >= q)
+    pairs = bench.tc_pairs(D, 3424)
+    assert pairs == D * (D + 1) // 2 + sum(s + 1 for s in range(3424, D - 1))
     prof = dict(tc_launches=10, tc_ms=2000.0, tc_mmas=1.0e6)
     r = bench.tensor_roofline(prof, N, n, min_rows, 100.0, 2)
-    want = 2.0 * D * D * upd * 2 / 2.0 / 1e12
+    want = 2.0 * pairs * upd * 2 / 2.0 / 1e12
     assert abs(r["achieved"] - want) < 1e-9 * want
     assert abs(r["frac"] - want / r["peak"]) < 1e-12
     assert abs(r["executed_tflops"] - 1.0e6 * 2 * 128 * 256 * 16 / 2.0 / 1e12) < 1e-9

@@ -82,3 +82,18 @@ def test_tensor_core_constants_match_the_header():
     for name in ("HK_TC_MIN_M", "HK_TC_AUTO_MIN_M", "HK_TC_MIN_ROWS", "HK_PRODUCT_TENSOR"):
         m = re.search(r"#define %s (\d+)" % name, text)
         assert m and int(m.group(1)) == getattr(hk, name), name
+
+
+def test_bench_short_product_cut_matches_the_kernel():
+    """bench.tc_cut restates TcShape::QCUT (csrc/tc.cuh) for the roofline's
+    algorithmic work: the same guard and the same formula at every width."""
+    import re
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    text = open(os.path.join(ROOT, "paper_1810_01478_gb300", "csrc", "tc.cuh")).read()
+    guard = int(re.search(r"static constexpr int GUARD = (\d+);", text).group(1))
+    assert re.search(r"static constexpr int QCUT = 32 \* \(\(n - GUARD - 2\) / 7\);", text)
+    for M in (8, 12, 16, 24):
+        n = 32 * M
+        assert bench.tc_cut(n) == 32 * ((n - guard - 2) // 7)
