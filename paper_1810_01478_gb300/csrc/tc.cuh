@@ -223,13 +223,16 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t taddr0, uint32_t taddr1, ui
 
 // acc += sum_u v[31 - u] 2^(7u) for the 32 positions of one group (v holds
 // the group's accumulator columns in reversed order), emitting its 7 limbs;
-// acc keeps the signed carry into the next limb.
+// acc keeps the signed carry into the next limb.  Coefficients are added in
+// pairs: |v_u + 128 v_(u+1)| < 129 * 2^24 < 2^31 fits 32 bits, which halves
+// the 64-bit additions; a pair spans at most one limb boundary (its
+// successor starts 14 bits higher), so at most one limb is emitted after it.
 __device__ __forceinline__ void tc_group_limbs(const uint32_t (&v)[32], long long& acc, uint32_t* lim) {
 #pragma unroll
-  for (int u = 0; u < 32; ++u) {
-    const int val = __float2int_rn(__uint_as_float(v[31 - u]));
-    acc += (long long)val * (1ll << ((7 * u) & 31));
-    if (((7 * (u + 1)) >> 5) != ((7 * u) >> 5)) {
+  for (int u = 0; u < 32; u += 2) {
+    const int w = __float2int_rn(__uint_as_float(v[31 - u])) + __float2int_rn(__uint_as_float(v[30 - u])) * 128;
+    acc += (long long)w * (1ll << ((7 * u) & 31));
+    if (((7 * (u + 2)) >> 5) != ((7 * u) >> 5)) {
       lim[(7 * u) >> 5] = (uint32_t)acc;
       acc >>= 32;
     }
