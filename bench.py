@@ -340,7 +340,14 @@ def tc_updates(N, min_rows):
     return tot
 
 
-def tensor_roofline(prof, N, n, min_rows, traffic_per_update, solves):
+def alg4_updates(N, k, min_rows):
+    """Algorithm 4's fused updates that run inside the tensor-core launches
+    when the block is planned (hk_plan_block): min(k, i) columns of the N - 1
+    - i rows below step i, for every step with at least min_rows rows."""
+    return sum(min(k, i) * (N - 1 - i) for i in range(N - 1) if N - 1 - i >= min_rows)
+
+
+def tensor_roofline(prof, N, n, min_rows, traffic_per_update, solves, k=0):
     """The roofline object of the tensor-core trailing update: algorithmic
     bf16 flops per second of its launches' device time, against the measured
     cuBLAS bf16 throughput sustained over a long run (the launches run inside
@@ -352,7 +359,8 @@ def tensor_roofline(prof, N, n, min_rows, traffic_per_update, solves):
     sec = prof["tc_ms"] / 1e3
     D, q = tc_digits(n), tc_cut(n)
     pairs = tc_pairs(D, q)
-    upd = tc_updates(N, min_rows) * solves  # the profile covers `solves` factorisations
+    # the profile covers `solves` factorisations, each with its planned Algorithm 4 steps
+    upd = (tc_updates(N, min_rows) + alg4_updates(N, k, min_rows)) * solves
     alg = 2.0 * pairs * upd
     executed = prof["tc_mmas"] * 2.0 * 128 * 256 * 16
     pk = measured_peaks()
@@ -408,7 +416,7 @@ def at_rule_bits(hk, stream, device, a, loss, need, lam_ref, sms, sm_max, rates,
     try:
         def solve():
             h.moments(1, 2, a.N, bits)
-            h.ldlt()
+            h.ldlt(k=a.k)
             h.inv_block(a.k)
             lam = h.lambda1(3)
             h.lambda1_grad()
@@ -466,7 +474,7 @@ def batch_times(hk, torch, probs, steps, warmup):
         for p in probs:
             with hk.Hankel(0) as h:
                 h.moments(*p["beta"], p["N"], p["bits"])
-                h.ldlt()
+                h.ldlt(k=p["k"])
                 h.inv_block(p["k"])
                 out.append(h.lambda1(1))
         return out
@@ -502,7 +510,7 @@ def run_ours(a):
 
     def step():
         h.moments(beta[0], beta[1], a.N, a.bits)
-        h.ldlt()
+        h.ldlt(k=a.k)
         h.inv_block(a.k)
         lam = h.lambda1(ne)
         gr = h.lambda1_grad()
@@ -561,7 +569,7 @@ def run_ours(a):
                     tc_traffic = t["bytes_per_update"]
             except (ValueError, KeyError):
                 tc_traffic = None
-        roofline = tensor_roofline(prof, a.N, n, hk.HK_TC_MIN_ROWS, tc_traffic, a.steps)
+        roofline = tensor_roofline(prof, a.N, n, hk.HK_TC_MIN_ROWS, tc_traffic, a.steps, k=a.k)
         roofline["ntt_steps"] = dict(note="the trailing launches of the last steps (fewer than "
                                           f"{hk.HK_TC_MIN_ROWS} rows) and the look-ahead entries keep NTT "
                                           "products; these figures cover every trailing launch",

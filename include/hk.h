@@ -132,6 +132,19 @@ HK_API hk_status hk_set_moments(hk_ctx* ctx, int N, int bits, const int32_t* sig
  * HK_ERR_NOT_PD by the next synchronising call. */
 HK_API hk_status hk_ldlt(hk_ctx* ctx);
 
+/* Declares the k of the hk_inv_block that follows the next hk_ldlt (0: no
+ * plan; the setting stays until changed).  With a plan, at widths and steps
+ * where the trailing update runs on the tensor cores (HK_TC_MIN_ROWS), the
+ * factorisation also runs those steps of Algorithm 4 (Sec. 4.4) inside the
+ * same launches: row i of X is final once step i - 1 has run, and step i's
+ * updates X[j][c] = trunc(X[j][c] - L[j][i] X[i][c]) use the digits of
+ * column i of L that the trailing update already holds.  hk_inv_block with the
+ * same k then runs only the remaining steps.  Every update is the same
+ * truncated operation, in the same order for each entry, so X and S are bit
+ * for bit those of the unplanned call.  0 <= k <= 64; a k above N is
+ * HK_ERR_ARG at hk_ldlt.  Enqueues nothing. */
+HK_API hk_status hk_plan_block(hk_ctx* ctx, int k);
+
 /* a5-a6. X = first k columns of L^{-1} by Algorithm 4 (Sec. 4.4; row
  * elimination, updates in increasing pivot order, one rounding each), then
  * S = (H_N^{-1})[0:k, 0:k], S_ab = sum_l X[l][a] X[l][b] / D_l (Sec. 4.4 eq.

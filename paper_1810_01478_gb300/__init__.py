@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 
 # every entry point declared in include/hk.h
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
-           "hk_ldlt", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
+           "hk_ldlt", "hk_plan_block", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
            "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run",
            "hk_set_product_algorithm", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"]
 HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT, HK_PRODUCT_TENSOR = 0, 1, 2, 3
@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
     L.hk_alu_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.hk_ldlt.argtypes = [_P]
     L.hk_inv_block.argtypes = [_P, ctypes.c_int]
+    L.hk_plan_block.argtypes = [_P, ctypes.c_int]
     L.hk_lambda1.argtypes = [_P, ctypes.c_int, _I32P, _I32P, _U32P, _F64P, _F64P]
     L.hk_lambda1_grad.argtypes = [_P, _I32P, _I32P, _U32P, _F64P]
     L.hk_export.argtypes = [_P, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, _I32P, _I32P, _U32P]
@@ -98,7 +99,7 @@ def load(path=LIB_PATH):
     L.hk_ldlt_noalloc.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 6 + [_P]
     L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
     for name in ("hk_set_product_algorithm", "hk_batch_run", "hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
-                 "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"):
+                 "hk_plan_block", "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -193,6 +194,11 @@ def hk_set_moments(ctx, N, bits, sign, exp, limbs, beta_num=0, beta_den=0):
 
 def hk_ldlt(ctx):
     _check(load().hk_ldlt(ctx), ctx)
+
+
+def hk_plan_block(ctx, k):
+    """Declare the k of the coming hk_inv_block (see include/hk.h)."""
+    _check(load().hk_plan_block(ctx, k), ctx)
 
 
 def hk_inv_block(ctx, k):
@@ -370,7 +376,11 @@ class Hankel:
         self.n = bits // 32
         hk_set_moments(self.ctx, N, bits, sign, exp, limbs, beta_num, beta_den)
 
-    def ldlt(self):
+    def ldlt(self, k=None):
+        """LDL^T; with k, Algorithm 4 for that k runs inside the tensor-core
+        steps (hk_plan_block) and inv_block(k) finishes it."""
+        if k is not None:
+            hk_plan_block(self.ctx, k)
         hk_ldlt(self.ctx)
 
     def inv_block(self, k):

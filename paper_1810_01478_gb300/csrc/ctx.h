@@ -70,6 +70,10 @@ struct Ctx {
   // undecided rows of the short-product launches: count, running total of
   // re-run items, then per-item records (Ops::tc_redo_ints)
   int* tc_redo = nullptr;
+  // hk_plan_block: the k whose Algorithm 4 steps the factorisation runs on
+  // the tensor cores, and after hk_ldlt the steps it ran (X holds their result)
+  int plan_k = 0;
+  int alg4_k = 0, alg4_done = 0;
   size_t tc_redo_ints = 0;
   double tc_mmas = 0.0;  // tcgen05.mma instructions of the profiled trailing launches (first launches)
   double tc_mmas_whole = 0.0;  // ... of one item of a re-run launch (whole product)

@@ -571,6 +571,9 @@ hk_status hk_ldlt(hk_ctx* h) {
   if (st != HK_OK) return st;
   Ctx& c = h->c;
   if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_ldlt before the moments");
+  if (c.plan_k > c.N) return set_error(c, HK_ERR_ARG, "the planned k exceeds N");
+  c.alg4_k = 0;
+  c.alg4_done = 0;
   const size_t pe0 = c.prof ? prof_mark(c) : 0;
   st = ops_for(c.M)->ldlt(c);
   if (st == HK_OK && (st = check_cuda(c, cudaMemsetAsync(c.d_err + 1, 0, sizeof(int), c.stream), "clearing")) == HK_OK) {
@@ -626,6 +629,15 @@ hk_status hk_precision_loss(hk_ctx* h, int32_t* loss_bits, int32_t* min_bits) {
   if ((st = read_loss(c, loss)) != HK_OK) return st;
   if (loss_bits) *loss_bits = loss;
   if (min_bits) *min_bits = min_bits_for(loss);
+  return HK_OK;
+}
+
+hk_status hk_plan_block(hk_ctx* h, int k) {
+  hk_status st = enter(h);
+  if (st != HK_OK) return st;
+  Ctx& c = h->c;
+  if (k < 0 || k > 64) return set_error(c, HK_ERR_ARG, "the planned k must be in 0..64");
+  c.plan_k = k;
   return HK_OK;
 }
 
@@ -821,6 +833,7 @@ static void run_instance(int device, hk_instance& in) {
     else
       st = hk_moments(h, in.beta_num, in.beta_den, in.N, in.bits);
   }
+  if (st == HK_OK) st = hk_plan_block(h, in.k);
   if (st == HK_OK) st = hk_ldlt(h);
   if (st == HK_OK) st = hk_inv_block(h, in.k);
   if (st == HK_OK)

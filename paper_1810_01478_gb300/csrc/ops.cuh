@@ -6,6 +6,7 @@
 
 #include "ctx.h"
 #include "k_ldlt.cuh"
+#include "k_tail.cuh"
 #include "tc.cuh"
 
 namespace hk {
@@ -320,10 +321,12 @@ struct Ops {
         return r;
       };
       int* const redo_before = c.tc_redo;
+      // U rows: the trailing update's columns, then k rows of X for Algorithm 4
+      const size_t max_items = (size_t)tc_trail_items(N, 0) + 64 * (size_t)((N + 127) / 128);
       if ((st = grow(c.tc_db, c.tc_db_cap, (size_t)S::ND * tc_pitch, 2)) ||
-          (st = grow(c.tc_du, c.tc_du_cap, (size_t)S::ND * N, 2)) ||
+          (st = grow(c.tc_du, c.tc_du_cap, (size_t)S::ND * (N + 64), 2)) ||
           (st = grow(c.tc_p, c.tc_p_cap, tc_p_words(tc_g), 4)) ||
-          (st = grow(c.tc_redo, c.tc_redo_ints, tc_redo_ints((size_t)tc_trail_items(N, 0)), 4)))
+          (st = grow(c.tc_redo, c.tc_redo_ints, tc_redo_ints(max_items), 4)))
         return st;
       // rows past N stay zero: they fill the last 128-row tile of a column;
       // the undecided-row records start clear (the running total only when
@@ -335,6 +338,19 @@ struct Ops {
         return st;
       c.tc_mmas_whole = tc_mmas_per_item(0);
     }
+    // Algorithm 4 for the planned k inside the tensor-core steps: X starts as
+    // the first k columns of the identity (hk_plan_block)
+    const int pk = tc ? c.plan_k : 0;
+    if (pk > 0) {
+      if (c.X.count != (int64_t)N * pk || c.X.n != n) {
+        dev_free(c.X);
+        if ((st = check_cuda(c, dev_alloc(c.X, (int64_t)N * pk, n), "allocating X")) != HK_OK) return st;
+      }
+      const int64_t work = (int64_t)N * pk * n;
+      k_x_init<M><<<(int)std::min<int64_t>((work + 255) / 256, 4096), 256, 0, c.stream>>>(c.X.view(), N, pk);
+      count_launch(c);
+    }
+    int alg4_steps = 0;
     uint32_t* FU = c.ntt_buf;
     uint32_t* FB = c.ntt_buf ? c.ntt_buf + per * (size_t)N : nullptr;
     uint32_t* FRD = c.ntt_buf ? c.ntt_buf + 2 * per * (size_t)N : nullptr;
@@ -409,6 +425,21 @@ struct Ops {
           tc_digits(c.U.mant, i + 1, (int)rows, i + 1, c.tc_du, 0, 0, c.device, s);
           tc_digits(c.A.mant, tri_pos(N, i + 1, i), (int)rows, i + 1, c.tc_db, 1, tc_pitch, c.device, s);
           count_launch(c, 2);
+          if (pk > 0) {
+            // Algorithm 4, step i: the copies X[j][i] = -L[j][i] (i < k), and
+            // the digits of row i of X (final since step i - 1) as U rows N + c
+            if (i < pk) {
+              k_alg4_copy<M><<<(int)std::min<int64_t>((rows + 3) / 4, 4 * sm_count(c.device)), 128, 0, s>>>(
+                  c.A.view(), c.X.view(), N, pk, i);
+              count_launch(c);
+            }
+            const int cols = std::min(pk, i);
+            if (cols > 0) {
+              tc_digits(c.X.mant, (int64_t)i * pk, cols, N, c.tc_du, 0, 0, c.device, s);
+              count_launch(c);
+            }
+            alg4_steps = i + 1;
+          }
         }
         if (i < (int)c.ev_col.size()) cudaEventRecord(c.ev_col[i], s);  // column i of L is final
       } else {
@@ -431,10 +462,17 @@ struct Ops {
         const size_t e1 = c.prof ? prof_mark(c) : 0;
         const bool tc_step = tc && rows >= HK_TC_MIN_ROWS;
         if (tc_step) {
-          const int items = tc_trail_items(N, i);
           const size_t cap = (c.tc_redo_ints - 4) / 6;
-          const cudaError_t e = tc_launch(TcTrail<M>{c.A.view(), c.U.view(), N, i}, items, c.tc_redo, cap, c.tc_db,
-                                          tc_pitch, c.tc_du, c.tc_p, tc_g, c.d_err, s);
+          const TcTrail<M> tr{c.A.view(), c.U.view(), N, i};
+          int items = tc_trail_items(N, i);
+          cudaError_t e;
+          if (pk > 0) {
+            items += std::min(pk, i) * (int)((rows + 127) / 128);
+            e = tc_launch(TcStep<M>{tr, c.X.view(), pk}, items, c.tc_redo, cap, c.tc_db, tc_pitch, c.tc_du, c.tc_p,
+                          tc_g, c.d_err, s);
+          } else {
+            e = tc_launch(tr, items, c.tc_redo, cap, c.tc_db, tc_pitch, c.tc_du, c.tc_p, tc_g, c.d_err, s);
+          }
           if ((st = check_cuda(c, e, "launching the tensor-core update")) != HK_OK) return st;
           count_launch(c);  // the re-run launch
           if (c.prof) {
@@ -452,6 +490,10 @@ struct Ops {
       count_launch(c, T > 1 ? 4 : 3);
     }
     cudaStreamWaitEvent(s, c.ev_recip, 0);  // the last pivot's check belongs to this call
+    if (alg4_steps > 0) {
+      c.alg4_k = pk;
+      c.alg4_done = alg4_steps;
+    }
     return check_cuda(c, cudaGetLastError(), "launching the factorisation");
   }
 

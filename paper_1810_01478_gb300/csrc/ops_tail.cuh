@@ -192,6 +192,9 @@ struct Tail {
       if ((st = check_cuda(c, dev_alloc(c.S, (int64_t)k * k, n), "allocating S")) != HK_OK) return st;
     }
     const bool ntt = use_ntt(M) && c.ntt_buf && c.ntt_cap >= 2 * (size_t)NTT_Q * ntt_len(n) * N;
+    // steps 0 .. alg4_done - 1 already ran inside the factorisation's
+    // tensor-core launches for this k (hk_plan_block): X holds their result
+    const int i0 = (c.alg4_done > 0 && c.alg4_k == k && c.X.count == (int64_t)N * k && c.X.n == n) ? c.alg4_done : 0;
     // Algorithm 4 beside the factorisation: on the low-priority stream a4,
     // step i after column i of L is marked (the LDL^T queued just before)
     const bool beside = ntt && c.cols_marked && c.a4 && c.ntt_buf2 &&
@@ -199,7 +202,7 @@ struct Tail {
     c.cols_marked = false;
     cudaStream_t xs = beside ? c.a4 : c.stream;
     if (beside) cudaStreamWaitEvent(xs, c.ev_ldlt_start, 0);
-    {
+    if (i0 == 0) {
       const int64_t work = (int64_t)N * k * n;
       const int grid = (int)std::min<int64_t>((work + 255) / 256, 4096);
       k_x_init<M><<<grid, 256, 0, xs>>>(c.X.view(), N, k);
@@ -219,7 +222,7 @@ struct Tail {
         return st;
       const int res = Ops<M>::resident_blocks(k_alg4_ntt<M>, 32 * NTW, tsm, c.device);
       const int fres = Ops<M>::resident_blocks(k_ntt_fwd<M>, 32 * W, fsm, c.device);
-      for (int i = 0; i < N - 1; ++i) {
+      for (int i = i0; i < N - 1; ++i) {
         const int cols = std::min(k, i);
         const int64_t per_row = cols + (i < k ? 1 : 0);
         const int64_t rows = N - 1 - i;
@@ -247,7 +250,7 @@ struct Tail {
       if ((st = check_cuda(c, allow_smem(k_alg4_step<M>, smem), "smem attribute")) != HK_OK) return st;
       const int res = Ops<M>::resident_blocks(k_alg4_step<M>, 32 * W, smem, c.device);
       // Algorithm 4: N-1 steps in increasing pivot order
-      for (int i = 0; i < N - 1; ++i) {
+      for (int i = i0; i < N - 1; ++i) {
         const int64_t per_row = std::min(k, i) + (i < k ? 1 : 0);
         const int64_t total = (int64_t)(N - 1 - i) * per_row;
         if (total == 0) continue;
@@ -256,6 +259,7 @@ struct Tail {
         count_launch(c);
       }
     }
+    c.alg4_done = 0;  // X now holds every step: a later call starts again from the identity
     if ((st = check_cuda(c, cudaGetLastError(), "Algorithm 4")) != HK_OK) return st;
     // reciprocals of the pivots (kept for the gradient), then Y[l][b] = X[l][b] / D_l
     DevVec* Rd = pool_get(c, "recip_d", N);

@@ -421,6 +421,73 @@ struct TcTrail {
   __device__ uint32_t take_rows(int, int) const { return 0xFFFFFFFFu; }
 };
 
+// Step i of Algorithm 1 together with step i of Algorithm 4 (Sec. 4.4):
+// X[j][c] = trunc(X[j][c] - L[j][i] X[i][c]) for j > i, c < min(k, i), with
+// the same digit rows L[j][i] as the trailing update and X[i][c] as the U
+// operand (its digits in U row N + c).  The Algorithm 4 items (column c, 128
+// rows of X from i + 1) come first, then the trailing items.
+template <int M>
+struct TcStep {
+  TcTrail<M> tr;
+  MPVec X;
+  int k;
+  __device__ int cols() const { return min(k, tr.i); }
+  __device__ int tiles4() const { return (tr.m() + 127) / 128; }
+  __device__ int items() const { return cols() * tiles4() + tr.items(); }
+  __device__ void item(int idx, int& ucol, int& row0, int& nrows) const {
+    const int n4 = cols() * tiles4();
+    if (idx >= n4) {
+      tr.item(idx - n4, ucol, row0, nrows);
+      return;
+    }
+    const int c = idx % cols(), kt = idx / cols();
+    ucol = tr.N + c;
+    row0 = tr.i + 1 + 128 * kt;
+    nrows = min(128, tr.m() - 128 * kt);
+  }
+  __device__ const uint32_t* addend(int ucol, int r) const {
+    if (ucol < tr.N) return tr.addend(ucol, r);
+    return X.mant + ((int64_t)r * k + (ucol - tr.N)) * (32 * M);
+  }
+  __device__ void operands(int ucol, int r, TcFused& f) const {
+    if (ucol < tr.N) {
+      tr.operands(ucol, r, f);
+      return;
+    }
+    constexpr int n = 32 * M;
+    const int c = ucol - tr.N;
+    const int64_t apos = (int64_t)r * k + c, xpos = (int64_t)tr.i * k + c, bpos = tri_pos(tr.N, r, tr.i);
+    f.amant = X.mant + apos * n;
+    f.asgn = X.sgn[apos];
+    f.aexp = X.exp[apos];
+    f.sx = X.sgn[xpos];
+    f.ex = X.exp[xpos];
+    f.xz = X.mant[xpos * n + n - 1] == 0u;
+    f.sy = tr.A.sgn[bpos];
+    f.ey = tr.A.exp[bpos];
+    f.yz = tr.A.mant[bpos * n + n - 1] == 0u;
+    f.out = X;
+    f.opos = apos;
+  }
+  static constexpr bool kRedo = false;
+  __device__ uint32_t take_rows(int, int) const { return 0xFFFFFFFFu; }
+};
+
+// Algorithm 4's copies X[j][i] = -L[j][i] (j > i) of a step i < k, one warp per row.
+template <int M>
+__global__ void k_alg4_copy(MPVec A, MPVec X, int N, int k, int i) {
+  constexpr int n = 32 * M;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int j = i + 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < N; j += nw) {
+    const int64_t fpos = tri_pos(N, j, i);
+    uint32_t v[M];
+    load_chunk<M>(A.mant + fpos * n, v);
+    const bool zero = __shfl_sync(FULL, v[M - 1], 31) == 0u;
+    Result r{zero ? 0 : (A.sgn[fpos] ^ 1), A.exp[fpos], zero};
+    store_result<M>(X, (int64_t)j * k + i, r, v);
+  }
+}
+
 // Elementwise out[e] = trunc(a[e] - x[e] y[e]): item e is U row e with the single digit row e.
 template <int M>
 struct TcBatch {

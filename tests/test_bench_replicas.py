@@ -125,6 +125,11 @@ def test_tensor_roofline_arithmetic():
     assert abs(r["frac"] - want / r["peak"]) < 1e-12
     assert abs(r["executed_tflops"] - 1.0e6 * 2 * 128 * 256 * 16 / 2.0 / 1e12) < 1e-9
     assert r["bound"] == "tensor" and abs(r["traffic"] - 100.0 * upd * 2 / 10) < 1e-6
+    # a planned block adds Algorithm 4's updates of the same steps
+    a4 = sum(min(32, i) * (N - 1 - i) for i in range(N - 1) if N - 1 - i >= min_rows)
+    assert bench.alg4_updates(N, 32, min_rows) == a4 > 0
+    r4 = bench.tensor_roofline(prof, N, n, min_rows, None, 2, k=32)
+    assert abs(r4["achieved"] - 2.0 * pairs * (upd + a4) * 2 / 2.0 / 1e12) < 1e-9 * r4["achieved"]
 
 
 def test_exact_lambda_comparison_helpers():

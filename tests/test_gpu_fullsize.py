@@ -146,6 +146,28 @@ def test_sweep_sizes(n_):
                     assert abs(value(s[j], e[j], m[j]) - want) / want < TOL, (n_, bits, j)
 
 
+def test_planned_block_at_the_widest_width():
+    """N = 320 at 24576 bits with hk_plan_block(k): the 64 steps with at least
+    256 trailing rows run Algorithm 4 inside their tensor-core launches; the
+    factor, X and lambda_1..3 equal the oracle's (tests/golden/w_320_24576)."""
+    import paper_1810_01478_gb300 as hk
+    from tests.digest import factor_digest, x_digest
+    gd = golden("w_320_24576")
+    N_, k_, bits = gd["N"], gd["k"], gd["bits"]
+    hk.load()
+    with hk.Hankel(0) as h:
+        h.moments(1, 2, N_, bits)
+        h.ldlt(k=k_)
+        h.inv_block(k_)
+        assert factor_digest(h, hk, N_) == gd["factor_sha256"]
+        assert x_digest(h, hk, N_, k_) == gd["x_sha256"]
+        s, e, m, _, _ = h.lambda1(3)
+        with mpm.workprec(2 * bits):
+            for j in range(3):
+                want = mpm.mpf(gd["lambdas"][j])
+                assert abs(value(s[j], e[j], m[j]) - want) / want < TOL, j
+
+
 @pytest.mark.parametrize("name", ["w_256_24576", "w_160_16384", "w_320_24576"])
 def test_widest_widths_whole_factor(name):
     """The whole factor and X bit for bit at 24576 bits (M = 24 limbs per

@@ -112,10 +112,15 @@ def hk_items(N, i):
     return s
 
 
-def test_tensor_full_factor_golden():
+@pytest.mark.parametrize("plan", [None, 32, 16])
+def test_tensor_full_factor_golden(plan):
     """beta = 1/2, N = 1024, 8192 bits: the whole factor and X against the
     oracle's digests (tests/golden/c5_1024_8192.json), tensor-core updates in
-    the 767 steps with at least 256 trailing rows."""
+    the 767 steps with at least 256 trailing rows.  plan = 32: Algorithm 4
+    runs inside those launches (hk_plan_block) and hk_inv_block(32) finishes
+    it; a second hk_inv_block(32) starts again from the identity.  plan = 16:
+    the planned k differs from the one asked for, and hk_inv_block runs every
+    step itself."""
     import json
     import os
     import paper_1810_01478_gb300 as hk
@@ -127,9 +132,12 @@ def test_tensor_full_factor_golden():
         hk.hk_set_product_algorithm(hk.HK_PRODUCT_TENSOR)
         with hk.Hankel(0) as h:
             h.moments(1, 2, 1024, 8192)
-            h.ldlt()
+            h.ldlt(k=plan)
             h.inv_block(32)
             assert factor_digest(h, hk, 1024) == gd["factor_sha256"]
             assert x_digest(h, hk, 1024, 32) == gd["x_sha256"]
+            if plan == 32:
+                h.inv_block(32)
+                assert x_digest(h, hk, 1024, 32) == gd["x_sha256"]
     finally:
         hk.hk_set_product_algorithm(hk.HK_PRODUCT_AUTO)
