@@ -227,11 +227,17 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t taddr0, uint32_t taddr1, ui
 // pairs: |v_u + 128 v_(u+1)| < 129 * 2^24 < 2^31 fits 32 bits, which halves
 // the 64-bit additions; a pair spans at most one limb boundary (its
 // successor starts 14 bits higher), so at most one limb is emitted after it.
+// The 64-bit additions are multiply-adds (acc += w * 2^s, s = 7u mod 32 <= 30
+// for even u), which run on the FMA pipe and leave the integer ALU, the
+// drain's busiest pipe, to the shifts of the limb emission.
 __device__ __forceinline__ void tc_group_limbs(const uint32_t (&v)[32], long long& acc, uint32_t* lim) {
 #pragma unroll
   for (int u = 0; u < 32; u += 2) {
-    const int w = __float2int_rn(__uint_as_float(v[31 - u])) + __float2int_rn(__uint_as_float(v[30 - u])) * 128;
-    acc += (long long)w * (1ll << ((7 * u) & 31));
+    int w;
+    asm("mad.lo.s32 %0, %1, 128, %2;"
+        : "=r"(w)
+        : "r"(__float2int_rn(__uint_as_float(v[30 - u]))), "r"(__float2int_rn(__uint_as_float(v[31 - u]))));
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(w), "r"(1 << ((7 * u) & 31)));
     if (((7 * (u + 2)) >> 5) != ((7 * u) >> 5)) {
       lim[(7 * u) >> 5] = (uint32_t)acc;
       acc >>= 32;
@@ -872,9 +878,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // the product (short or whole) is in [0, 2^(64 n)): the limbs past
         // 2n and the last carry are zero
         uint32_t stray = (t == TT - 1) ? (uint32_t)(acc != 0) : 0u;
+        if (L0 + 56 * t + 55 >= 2 * n) {  // only the last tiles reach limb 2n
 #pragma unroll
-        for (int w = 0; w < 56; ++w)
-          if (L0 + 56 * t + w >= 2 * n) stray |= lim[w];
+          for (int w = 0; w < 56; ++w)
+            if (L0 + 56 * t + w >= 2 * n) stray |= lim[w];
+        }
         if (stray) atomicOr(err, ERR_LOOP);
       }
       if (!ok) break;
