@@ -473,9 +473,11 @@ __device__ __forceinline__ Result combine(const Staged& X, int sX, const Staged&
 
 // combine() on a frame of one chunk of MC limbs per lane (32 MC limbs,
 // n = 32 M < 32 MC), for operands that both lie inside it, with the
-// short-product test always on (chk >= 1, see combine()).  The carry or
-// borrow between the lanes' chunks is resolved with one 32-bit ballot per
-// kind and a 64-bit prefix sum whose bit 32 is the carry out of the frame.
+// short-product test on when chk >= 1 (see combine()) and off for chk < 0
+// (an exact frame, such as combine()'s stand-in for an operand wholly below
+// the other).  The carry or borrow between the lanes' chunks is resolved
+// with one 32-bit ballot per kind and a 64-bit prefix sum whose bit 32 is
+// the carry out of the frame.
 template <int MC, int M, class IX>
 __device__ __forceinline__ Result combine_narrow(const Staged& X, int sX, const Staged& Y, int sY, int base,
                                                  uint32_t* fr, uint32_t (&out)[M], int chk) {
@@ -486,18 +488,36 @@ __device__ __forceinline__ Result combine_narrow(const Staged& X, int sX, const 
   uint32_t top = 0;
   int rs = sX;
   {
-    uint32_t xv[MC], yv[MC];
-    frame_chunk<MC, IX>(X, lane, xv);
-    frame_chunk<MC, IX>(Y, lane, yv);
+    // r = X's chunk, then Y's elements added or subtracted one by one along
+    // the carry chain (Y's chunk is never held whole)
+    frame_chunk<MC, IX>(X, lane, r);
+    auto yel = [&](int k) -> uint32_t {
+      const int i = lane * MC + k - Y.off;
+      if (Y.p) return (i >= 0 && i < Y.len) ? Y.p[IX::at(i)] : 0u;
+      return i == 0 ? 1u : 0u;
+    };
+    uint32_t cy;
     if (sX == sY) {
-      const bool g = chunk_add<MC>(r, xv, yv) != 0;
+      asm volatile("add.cc.u32 %0, %0, %1;" : "+r"(r[0]) : "r"(yel(0)));
+#pragma unroll
+      for (int k = 1; k < MC; ++k) asm volatile("addc.cc.u32 %0, %0, %1;" : "+r"(r[k]) : "r"(yel(k)));
+      asm volatile("addc.u32 %0, 0, 0;" : "=r"(cy));
+    } else {
+      asm volatile("sub.cc.u32 %0, %0, %1;" : "+r"(r[0]) : "r"(yel(0)));
+#pragma unroll
+      for (int k = 1; k < MC; ++k) asm volatile("subc.cc.u32 %0, %0, %1;" : "+r"(r[k]) : "r"(yel(k)));
+      asm volatile("subc.u32 %0, 0, 0;" : "=r"(cy));
+      cy &= 1u;
+    }
+    if (sX == sY) {
+      const bool g = cy != 0;
       const bool p = !g && chunk_is_ones<MC>(r);
       const uint64_t G = __ballot_sync(FULL, g), A = G | __ballot_sync(FULL, p);
       const uint64_t C = (A + G) ^ A ^ G;  // carry into chunk l is bit l, out of the frame bit 32
       if ((C >> lane) & 1) chunk_add_word<MC>(r, 1u);
       top = (uint32_t)(C >> 32) & 1u;
     } else {
-      const bool g = chunk_sub<MC>(r, xv, yv) != 0;
+      const bool g = cy != 0;
       const bool p = !g && chunk_is_zero<MC>(r);
       const uint64_t G = __ballot_sync(FULL, g), A = G | __ballot_sync(FULL, p);
       const uint64_t B = (A + G) ^ A ^ G;  // borrow into chunk l is bit l
@@ -523,14 +543,14 @@ __device__ __forceinline__ Result combine_narrow(const Staged& X, int sX, const 
 #pragma unroll
     for (int k = 0; k < M; ++k) out[k] = 0;
     res.sgn = 0; res.exp = 0; res.zero = true;
-    res.amb = true;  // a zero short difference says nothing about the exact one
+    res.amb = chk >= 0;  // a zero short difference says nothing about the exact one
     return res;
   } else {
     const int h = 31 - __clz((int)NZ);
     const int kk = __shfl_sync(FULL, chunk_top<MC>(r), h);
     T = h * MC + kk;
   }
-  {
+  if (chk >= 0) {
     const int last = T - n + 1;
     bool nz = false, nf = false;
 #pragma unroll
@@ -552,7 +572,7 @@ __device__ __forceinline__ Result combine_narrow(const Staged& X, int sX, const 
   for (int k = 0; k < MC; ++k) fr[IX::at(lane * MC + k)] = r[k];
   if (lane == 0) fr[IX::at(W)] = top;
   __syncwarp();
-  const int lowest = T - n + 1;  // >= chk + 1 once the test has passed
+  const int lowest = T - n + 1;  // >= chk + 1 once the test has passed, >= 0 for an exact frame
 #pragma unroll
   for (int k = 0; k < M; ++k) out[k] = fr[IX::at(lowest + lane * M + k)];
   __syncwarp();

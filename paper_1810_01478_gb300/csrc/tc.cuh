@@ -892,7 +892,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int ucol, row0, nrows;
       items.item(it, ucol, row0, nrows);
       const uint32_t rows = items.take_rows(it, q);
-      const int lc = Q > 0 ? L0 + 2 : -1;  // the omitted terms are below 2^(7Q + 18) < 2^(32 (L0 + 1))
       uint32_t undecided = 0;
       // the next row's addend and product limbs are brought into L2 while
       // this one is formed: one row's loads are otherwise all latency
@@ -937,16 +936,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // are below 2^(32 F0 + 1) + 2^(32 L0 + 18), under frame limb
         // max(L0 - F0, 0) + 2.  A product wholly below the addend (d > 2n)
         // goes through the exact stand-in of sub_product instead.
+        // A product wholly below the addend (d > 2n) changes the truncated
+        // result only through its sign (combine()'s stand-in: a single 1
+        // two limbs below the addend's last limb gives the same result), on
+        // the same frame with the test off.  The re-run launch forms whole
+        // products and takes the general frame (sub_product).
         const long long d = (long long)f.aexp - (long long)(f.ex + f.ey);
         Result res;
-        if (lc >= 0 && !p_zero && d <= 2 * n) {
-          const int F0 = (int)max((long long)n - 32, (a_zero ? (long long)n : d) - 32);
-          const bool a_out = a_zero || d - F0 < -(long long)n;  // the addend wholly below the frame
-          res = combine_narrow<M + 1, M, IxPad>(Staged{sm.sa, a_out ? 0 : (int)(d - F0), a_out ? 0 : n}, f.asgn,
-                                                Staged{sm.sp, -F0, 2 * n}, f.sx ^ f.sy ^ 1, f.ex + f.ey + F0, sm.sa,
-                                                o, max(L0 - F0, 0) + 2);
+        if constexpr (!Items::kRedo) {
+          if (p_zero) {  // the result is a itself
+#pragma unroll
+            for (int w = 0; w < M; ++w) o[w] = sm.sa[IxPad::at(lane * M + w)];
+            __syncwarp();
+            res.zero = a_zero;
+            res.sgn = a_zero ? 0 : f.asgn;
+            res.exp = a_zero ? 0 : f.aexp;
+          } else if (d <= 2 * n) {
+            const int F0 = (int)max((long long)n - 32, (a_zero ? (long long)n : d) - 32);
+            const bool a_out = a_zero || d - F0 < -(long long)n;  // the addend wholly below the frame
+            res = combine_narrow<M + 1, M, IxPad>(Staged{sm.sa, a_out ? 0 : (int)(d - F0), a_out ? 0 : n},
+                                                  f.asgn, Staged{sm.sp, -F0, 2 * n}, f.sx ^ f.sy ^ 1,
+                                                  f.ex + f.ey + F0, sm.sa, o, max(L0 - F0, 0) + 2);
+          } else {
+            res = combine_narrow<M + 1, M, IxPad>(Staged{sm.sa, 32, n}, f.asgn, Staged{nullptr, 30, 1},
+                                                  f.sx ^ f.sy ^ 1, f.aexp - 32, sm.sa, o, -1);
+          }
         } else {
-          res = sub_product<M, IxPad, true>(sm, f.asgn, f.aexp, a_zero, f.sx ^ f.sy, f.ex + f.ey, p_zero, o, lc);
+          res = sub_product<M, IxPad>(sm, f.asgn, f.aexp, a_zero, f.sx ^ f.sy, f.ex + f.ey, p_zero, o);
         }
         if (res.amb) undecided |= 1u << j;
         else store_result<M>(f.out, f.opos, res, o);
