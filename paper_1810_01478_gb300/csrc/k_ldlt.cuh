@@ -354,8 +354,14 @@ __device__ __forceinline__ Result fused_ntt(uint32_t* nb, const NttConst& nc, co
 // FU[r - i - 1] = F(A[r][i]) (unscaled; the trailing update reuses it),
 // FRD = F(R) then F(D) (scaled), FQ[r - i - 1]: scratch for F(Q~) (the slot
 // that F(B_i[r]) takes afterwards).
+// Blocks of HK_SCALE_WARPS warps, two per SM: the exact quotient's
+// correction holds several n-limb chunks at once, and the 255 registers a
+// thread gets at that size keep it out of local memory.
+#ifndef HK_SCALE_WARPS
+#define HK_SCALE_WARPS 4
+#endif
 template <int M>
-__global__ void __launch_bounds__(32 * HK_NTT_TRAIL_WARPS, 2)
+__global__ void __launch_bounds__(32 * HK_SCALE_WARPS, 2)
     k_scale_ntt(MPVec A, MPVec U, int N, int i, const uint32_t* __restrict__ FU, const uint32_t* __restrict__ FRD,
                 uint32_t* FQ, const int* rec_meta, NttConst nc, int* err) {
   constexpr int n = 32 * M;

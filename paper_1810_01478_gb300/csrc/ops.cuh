@@ -271,7 +271,7 @@ struct Ops {
     // NTT products: transforms of U and B_i once per step, reused by every update
     const bool ntt = use_ntt(M);
     NttConst nc{};
-    size_t per = 0, ntt_smem = 0, fwd_smem = 0;
+    size_t per = 0, ntt_smem = 0, fwd_smem = 0, scale_smem = 0;
     int ntt_res = 0, fwd_res = 0, scale_ntt_res = 0;
     if (ntt) {
       nc = ntt_const(n);
@@ -288,6 +288,7 @@ struct Ops {
         c.ntt_cap = need;
       }
       ntt_smem = (size_t)NTW * NTT_Q * ntt_stride(nc.L) * 4;
+      scale_smem = (size_t)HK_SCALE_WARPS * NTT_Q * ntt_stride(nc.L) * 4;
       fwd_smem = (size_t)WARPS * ntt_stride(nc.L) * 4;
       if ((st = check_cuda(c, allow_smem(k_trailing_ntt<M>, ntt_smem), "smem attribute")) ||
           (st = check_cuda(c, allow_smem(k_ntt_fwd<M>, fwd_smem), "smem attribute")))
@@ -299,8 +300,8 @@ struct Ops {
         return st;
       ntt_res = resident_blocks(k_trailing_ntt<M>, 32 * NTW, ntt_smem, c.device);
       fwd_res = resident_blocks(k_ntt_fwd<M>, 32 * WARPS, fwd_smem, c.device);
-      if ((st = check_cuda(c, allow_smem(k_scale_ntt<M>, ntt_smem), "smem attribute")) != HK_OK) return st;
-      scale_ntt_res = resident_blocks(k_scale_ntt<M>, 32 * NTW, ntt_smem, c.device);
+      if ((st = check_cuda(c, allow_smem(k_scale_ntt<M>, scale_smem), "smem attribute")) != HK_OK) return st;
+      scale_ntt_res = resident_blocks(k_scale_ntt<M>, 32 * HK_SCALE_WARPS, scale_smem, c.device);
     }
     // tensor-core products: digit matrices and the blocks' product buffers
     const bool tc = ntt && kTc && use_tc(M);
@@ -412,8 +413,8 @@ struct Ops {
         // through transforms; then F(B_i[r]) for the update
         const int g = (int)std::min<int64_t>((rows + WARPS - 1) / WARPS, fwd_res);
         k_ntt_fwd<M><<<g, 32 * WARPS, fwd_smem, s>>>(c.A.view(), tri_pos(N, i + 1, i), (int)rows, FU, nc, 0);
-        const int gq = (int)std::min<int64_t>((rows + NTW - 1) / NTW, scale_ntt_res);
-        k_scale_ntt<M><<<gq, 32 * NTW, ntt_smem, s>>>(c.A.view(), c.U.view(), N, i, FU, FRD, FB, c.rec_meta, nc,
+        const int gq = (int)std::min<int64_t>((rows + HK_SCALE_WARPS - 1) / HK_SCALE_WARPS, scale_ntt_res);
+        k_scale_ntt<M><<<gq, 32 * HK_SCALE_WARPS, scale_smem, s>>>(c.A.view(), c.U.view(), N, i, FU, FRD, FB, c.rec_meta, nc,
                                                        c.d_err);
         // with tensor-core products only the look-ahead entry (i+1, i+1) needs F(B_i)
         const bool tc_step = tc && rows >= HK_TC_MIN_ROWS;
