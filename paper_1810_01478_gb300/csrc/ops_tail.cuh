@@ -397,8 +397,96 @@ struct Tail {
     return s;
   }
 
+  // Eigenvalues of a symmetric kk x kk matrix (row stride kk) by cyclic
+  // Jacobi rotations, in double precision; descending.  Empty on failure.
+  static std::vector<double> jacobi_eigenvalues(std::vector<double> a, int kk) {
+    for (int sweep = 0; sweep < 60; ++sweep) {
+      double off = 0, tot = 0;
+      for (int i = 0; i < kk; ++i)
+        for (int j = 0; j < kk; ++j) {
+          tot += a[i * kk + j] * a[i * kk + j];
+          if (i != j) off += a[i * kk + j] * a[i * kk + j];
+        }
+      if (!std::isfinite(tot)) return {};
+      if (off <= 1e-60 * tot) break;
+      for (int p = 0; p < kk; ++p)
+        for (int q = p + 1; q < kk; ++q) {
+          const double apq = a[p * kk + q];
+          if (apq == 0.0) continue;
+          const double th = (a[q * kk + q] - a[p * kk + p]) / (2 * apq);
+          const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1));
+          const double cs = 1 / std::sqrt(t * t + 1), sn = t * cs;
+          for (int r = 0; r < kk; ++r) {  // columns p, q
+            const double x = a[r * kk + p], y = a[r * kk + q];
+            a[r * kk + p] = cs * x - sn * y;
+            a[r * kk + q] = sn * x + cs * y;
+          }
+          for (int r = 0; r < kk; ++r) {  // rows p, q
+            const double x = a[p * kk + r], y = a[q * kk + r];
+            a[p * kk + r] = cs * x - sn * y;
+            a[q * kk + r] = sn * x + cs * y;
+          }
+        }
+    }
+    std::vector<double> ev(kk);
+    for (int i = 0; i < kk; ++i) ev[i] = a[i * kk + i];
+    std::sort(ev.begin(), ev.end(), [](double x, double y) { return x > y; });
+    return ev;
+  }
+
+  // Squarings before eig_top first tests convergence, per eigenvalue m < ne
+  // of the leading kk block: after s squarings the quotient's error is about
+  // (nu_{m+1}/nu_m)^(2^(s+1)), so a double-precision estimate of the block's
+  // spectrum gives the least s that reaches bits_target.  It only moves the
+  // first test: eig_top squares on until two successive quotients agree, so
+  // an estimate that is off costs time, not accuracy.  Never more than the
+  // rule that assumes a ratio of 1/2 (squarings_for), which is also taken
+  // when the estimate fails or the ratio is not below 1/2.
+  static std::vector<int> squarings_est(Ctx& c, int kk, int ne, int bits_target) {
+    const int k = c.k;
+    std::vector<int> s(ne, squarings_for(bits_target));
+    const size_t kk2 = (size_t)k * k;
+    std::vector<int32_t> sg(kk2), ex(kk2);
+    std::vector<uint32_t> top(3 * kk2);
+    if (cudaMemcpyAsync(sg.data(), c.S.sgn, kk2 * 4, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+        cudaMemcpyAsync(ex.data(), c.S.exp, kk2 * 4, cudaMemcpyDeviceToHost, c.stream) != cudaSuccess ||
+        cudaMemcpy2DAsync(top.data(), 12, c.S.mant + (n - 3), (size_t)n * 4, 12, kk2, cudaMemcpyDeviceToHost,
+                          c.stream) != cudaSuccess ||
+        cudaStreamSynchronize(c.stream) != cudaSuccess) {
+      cudaGetLastError();
+      return s;
+    }
+    int emax = INT_MIN;
+    for (int a = 0; a < kk; ++a)
+      for (int b = 0; b < kk; ++b)
+        if (top[3 * ((size_t)a * k + b) + 2]) emax = std::max(emax, ex[(size_t)a * k + b]);
+    if (emax == INT_MIN) return s;
+    std::vector<double> m2((size_t)kk * kk);
+    for (int a = 0; a < kk; ++a)
+      for (int b = 0; b < kk; ++b) {
+        const size_t e = (size_t)a * k + b;
+        const double v = ((double)top[3 * e + 2] * 4294967296.0 + (double)top[3 * e + 1]) * 4294967296.0 +
+                         (double)top[3 * e];
+        const double x = std::ldexp(v, 32 * (ex[e] - emax) - 64);  // scaled by 2^(-32 (emax + n - 1))
+        m2[(size_t)a * kk + b] = sg[e] ? -x : x;
+      }
+    const std::vector<double> ev = jacobi_eigenvalues(m2, kk);
+    if ((int)ev.size() != kk) return s;
+    for (int m = 0; m < ne; ++m) {
+      if (!(ev[m] > 0)) break;
+      const double r = m + 1 < kk ? std::max(ev[m + 1], 0.0) / ev[m] : 0.0;
+      if (!(r < 0.5)) continue;
+      const double need = r > 0 ? (double)bits_target / -std::log2(r) : 1.0;
+      int sm = 1;
+      while ((double)(1 << (sm + 1)) < need && sm < s[m]) ++sm;
+      s[m] = std::min(s[m], sm);
+    }
+    return s;
+  }
+
   // eigenvalues of the leading kk block: lam[m] = 1/nu_m (m < ne) into LAM[m]
-  static hk_status block_lambdas(Ctx& c, int kk, int ne, int s, int tol, MPVec LAM, bool keep_vector) {
+  static hk_status block_lambdas(Ctx& c, int kk, int ne, const std::vector<int>& s, int tol, MPVec LAM,
+                                 bool keep_vector) {
     const int k = c.k;
     DevVec* Sw = pool_get(c, "Sw", (int64_t)k * k);
     DevVec* V = pool_get(c, "v", k);
@@ -411,7 +499,7 @@ struct Tail {
     for (int64_t e = 0; e < (int64_t)k * k; ++e) cp.push_back(ChainTask{e, e, 0, 0, 0, 0, 0, 0});
     if ((st = chains(c, cp, c.S.view(), c.S.view(), c.S.view(), Sw->view())) != HK_OK) return st;
     for (int m = 0; m < ne; ++m) {
-      if ((st = eig_top(c, Sw->view(), k, kk, s, tol, V->view(), *scal, 2 * m)) != HK_OK) return st;
+      if ((st = eig_top(c, Sw->view(), k, kk, s[m], tol, V->view(), *scal, 2 * m)) != HK_OK) return st;
       if (m == 0 && keep_vector) {
         DevVec* E1 = pool_get(c, "eig1", 2);  // nu_1, v^T v
         if (!E1) return c.sticky;
@@ -445,12 +533,15 @@ struct Tail {
     DevVec* DIF = pool_get(c, "lam_diff", 3);
     if (!LAM || !LAM1 || !DIF) return c.sticky;
     // lambda to the working precision (agreement to n - 3 limbs) ...
-    if ((st = block_lambdas(c, k, n_eig, squarings_for(32 * n + 64), n - 3, LAM->view(), true)) != HK_OK) return st;
+    if ((st = block_lambdas(c, k, n_eig, squarings_est(c, k, n_eig, 32 * n + 64), n - 3, LAM->view(), true)) !=
+        HK_OK)
+      return st;
     const int ne1 = std::min(n_eig, k - 1);
     if (ne1 > 0) {
       // the (k-1) x (k-1) estimate only feeds a double-precision difference
       // ... the (k-1) estimate only to ~640 bits (it feeds a double-precision difference)
-      if ((st = block_lambdas(c, k - 1, ne1, squarings_for(640), std::min(n - 3, 20), LAM1->view(), false)) != HK_OK)
+      if ((st = block_lambdas(c, k - 1, ne1, squarings_est(c, k - 1, ne1, 640), std::min(n - 3, 20), LAM1->view(),
+                              false)) != HK_OK)
         return st;
       DevVec* ONE = one(c);
       if (!ONE) return c.sticky;
