@@ -65,3 +65,12 @@ def test_noalloc_argument_checks_need_no_device():
     words = 1 << 20
     assert 1360 * 770 + 768 + 35 <= words < 1361 * 770 + 768 + 32
     assert L.hk_ldlt_noalloc(24576, 1361, *nulls, None) == hk.HK_ERR_ARG
+
+
+def test_plan_block_needs_a_context():
+    """hk_plan_block, like every context call, answers HK_ERR_ARG for a null
+    context before it touches a device."""
+    import paper_1810_01478_gb300 as hk
+    L = hk.load()
+    assert L.hk_plan_block(None, 32) == hk.HK_ERR_ARG
+    assert L.hk_plan_block(None, 0) == hk.HK_ERR_ARG
