@@ -11,7 +11,6 @@
 // scratch from one fixed array in device memory, declared below, so a call
 // makes no allocation at all; the caller still passes the moments and the
 // factor buffer.
-#include <mutex>
 
 #include "ctx.h"
 #include "widths.h"
@@ -25,26 +24,13 @@ namespace {
 constexpr size_t kScratchWords = HK_NOALLOC_SCRATCH_WORDS;
 static __device__ __align__(256) uint32_t hk_noalloc_scratch[kScratchWords];
 
-// Host code cannot use the array's name as a device address; the address is
-// looked up once per device (with that device current) and cached here.  The
-// cache lives as long as the library: a cudaDeviceReset (or anything else
-// that unloads the device's module) while the library stays loaded would
-// leave a stale address here, so the library does not support that.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-uint32_t* g_scratch[kMaxDevices] = {};
-
+// Host code cannot use the array's name as a device address: the address is
+// looked up on every call (with the caller's device current), so nothing
+// goes stale when a device is reset and the module reloaded.
 hk_status scratch_for_current_device(uint32_t** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return HK_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return HK_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, hk_noalloc_scratch) != cudaSuccess || !p) return HK_ERR_CUDA;
-    g_scratch[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = g_scratch[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, hk_noalloc_scratch) != cudaSuccess || !p) return HK_ERR_CUDA;
+  *out = static_cast<uint32_t*>(p);
   return HK_OK;
 }
 
