@@ -448,17 +448,81 @@ def at_rule_bits(hk, stream, device, a, loss, need, lam_ref, sms, sm_max, rates,
 
 
 def batch_summary(hk, torch, steps=2):
-    """The batched configuration's 16 instances through hk_batch_run
-    (concurrent streams: one context, stream and host thread per instance)
-    against the same instances one after another on one stream."""
+    """The batched configuration's 16 instances through hk_batch_run (the
+    instances of each width up to 8192 bits in one persistent launch,
+    hk_ldlt_batch; the 12288-bit ones on their own streams) against the same
+    instances one after another on one stream; and a sweep of 32 instances
+    at one width whose factorisations run in one persistent launch, beside
+    concurrent streams and one stream."""
     probs = [dict(beta=(1, m), N=N, k=16, bits=32 * N, n_eig=1) for m in (1, 2, 3, 4) for N in (128, 192, 256, 384)]
     t = batch_times(hk, torch, probs, steps, 1)
-    return dict(instances=len(probs), form="concurrent streams (one context, stream and host thread per instance), "
-                                           "not one persistent launch",
+    return dict(instances=len(probs),
+                form="hk_batch_run: one persistent launch per width up to 8192 bits (hk_ldlt_batch), "
+                     "the wider instances on concurrent streams",
                 workload="beta=1/m, m in {1,2,3,4} x N in {128,192,256,384}, k=16, 32N bits, moments -> LDL^T -> "
                          "block -> lambda_1",
                 seconds_batched=t["batched"], seconds_sequential=t["sequential"],
-                speedup=t["sequential"] / t["batched"], instances_per_hour=3600.0 * len(probs) / t["batched"])
+                speedup=t["sequential"] / t["batched"], instances_per_hour=3600.0 * len(probs) / t["batched"],
+                sweep=ldlt_sweep_times(hk, torch))
+
+
+def ldlt_sweep_times(hk, torch, bits=4096, ns=(96, 128, 160, 192, 224, 256, 288, 320), reps=3):
+    """Seconds for the factorisations of 32 instances (beta = 1/m, m = 1..4,
+    x ns) at one width: one persistent launch (hk_ldlt_batch), one stream
+    and host thread per instance (hk_ldlt on each), and one stream; the best
+    of `reps` runs each, from the moments to the last pivot on the host."""
+    import threading
+    sp = [((1, m), N) for m in (1, 2, 3, 4) for N in ns]
+
+    def persistent():
+        hs = [hk.Hankel(0) for _ in sp]
+        t0 = time.perf_counter()
+        for (b, N), h in zip(sp, hs):
+            h.moments(b[0], b[1], N, bits)
+        hk.hk_ldlt_batch([h.ctx for h in hs])
+        for (b, N), h in zip(sp, hs):
+            h.export(hk.HK_D, N - 1, 1)
+        dt = time.perf_counter() - t0
+        for h in hs:
+            h.close()
+        return dt
+
+    def streams():
+        ss = [torch.cuda.Stream() for _ in sp]
+        hs = [hk.Hankel(0, s.cuda_stream) for s in ss]
+
+        def one(q):
+            (b, N), h = sp[q], hs[q]
+            h.moments(b[0], b[1], N, bits)
+            h.ldlt()
+            h.export(hk.HK_D, N - 1, 1)
+        t0 = time.perf_counter()
+        th = [threading.Thread(target=one, args=(q,)) for q in range(len(sp))]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        dt = time.perf_counter() - t0
+        for h in hs:
+            h.close()
+        return dt
+
+    def one_stream():
+        t0 = time.perf_counter()
+        for b, N in sp:
+            with hk.Hankel(0) as h:
+                h.moments(b[0], b[1], N, bits)
+                h.ldlt()
+                h.export(hk.HK_D, N - 1, 1)
+        return time.perf_counter() - t0
+
+    out = dict(workload=f"LDL^T of 32 instances: beta=1/m, m in 1..4 x N in {list(ns)}, {bits} bits")
+    for name, fn in (("persistent_launch", persistent), ("concurrent_streams", streams), ("one_stream", one_stream)):
+        fn()
+        out["seconds_" + name] = min(fn() for _ in range(reps))
+    out["speedup_vs_streams"] = out["seconds_concurrent_streams"] / out["seconds_persistent_launch"]
+    out["speedup_vs_one_stream"] = out["seconds_one_stream"] / out["seconds_persistent_launch"]
+    return out
 
 
 def batch_times(hk, torch, probs, steps, warmup):
@@ -630,9 +694,9 @@ def profile_case(a):
 
 def run_batch(a):
     """The batched form alone: 16 instances of uneven size through
-    hk_batch_run (concurrent streams: one context, stream and host thread
-    each), timed beside the same instances solved one after another on one
-    stream.  beta = 1/m (moments exact on the device) with m in {1, 2, 3, 4},
+    hk_batch_run (one persistent launch per width up to 8192 bits, the rest
+    on concurrent streams), timed beside the same instances solved one after
+    another on one stream, plus the 32-instance factorisation sweep.  beta = 1/m (moments exact on the device) with m in {1, 2, 3, 4},
     N in {128, 192, 256, 384}, k = 16, 32 N bits: the shapes of the
     paper-scale batched configuration."""
     import torch
@@ -640,7 +704,7 @@ def run_batch(a):
     g.build()
     import paper_1810_01478_gb300 as hk
     out = batch_summary(hk, torch, steps=a.steps)
-    print(json.dumps(dict(metric="instances/hour (16 uneven lambda_1 solves, concurrent streams)",
+    print(json.dumps(dict(metric="instances/hour (16 uneven lambda_1 solves, hk_batch_run)",
                           value=out["instances_per_hour"], unit="instances/hour", n_gpus=1, steps=a.steps,
                           warmup=a.warmup, higher_is_better=True, data="synthetic", **out)), flush=True)
 

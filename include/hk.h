@@ -241,6 +241,8 @@ HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 #define HK_PRODUCT_TENSOR 3
 #define HK_NTT_AUTO_MIN_M 8
 #define HK_TC_MIN_M 8
+/* widest width of hk_ldlt_batch: 1024 * HK_BATCH_MAX_M bits */
+#define HK_BATCH_MAX_M 8
 #define HK_TC_AUTO_MIN_M 12
 /* With tensor-core products, steps of Algorithm 1 whose trailing triangle has
  * fewer rows than this keep NTT products (too few 128-row work items to fill
@@ -267,12 +269,15 @@ HK_API hk_status hk_div_batch(int bits, int64_t count, const int32_t* a_sign, co
 
 /* a9. Batched form: `count` independent instances (uneven beta, N, k, bits)
  * solved concurrently on one device, each on its own stream and context,
- * driven by up to `max_concurrent` host threads (0 = all at once).  Per
- * instance: moments on the device when mu_* are NULL (beta = 1/m), else
- * imported from the host arrays; then hk_ldlt, hk_inv_block(k) and
- * hk_lambda1(n_eig).  Results and the instance's own status are written into
- * its struct; the call returns HK_OK when every instance succeeded, else the
- * first failing instance's status. */
+ * in waves of up to `max_concurrent` instances (0 = all in one wave), each
+ * wave driven by as many host threads.  Per instance: moments on the device
+ * when mu_* are NULL (beta = 1/m), else imported from the host arrays; then
+ * the factorisation: the wave's instances of one width up to
+ * HK_BATCH_MAX_M * 1024 bits, when there are two or more, share one
+ * persistent launch (hk_ldlt_batch), every other instance runs hk_ldlt;
+ * then hk_inv_block(k) and hk_lambda1(n_eig).  Results and the instance's
+ * own status are written into its struct; the call returns HK_OK when every
+ * instance succeeded, else the first failing instance's status. */
 typedef struct hk_instance {
   int64_t beta_num, beta_den;
   int32_t N, k, bits, n_eig;
@@ -294,6 +299,43 @@ typedef struct hk_instance {
 } hk_instance;
 HK_API hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_concurrent);
 
+/* a9. Algorithm 1 (Sec. 4.3) for `count` contexts in ONE persistent launch.
+ * Every context must be on one device, at one width of at most
+ * HK_BATCH_MAX_M * 1024 bits (else HK_ERR_ARG / HK_ERR_UNSUPPORTED), with
+ * its moments set (else HK_ERR_ORDER), and appear once.  Each instance's
+ * factorisation is a chain of phases (the pivot's reciprocal, the column
+ * scale, the trailing update of each step); the launch's warps take work
+ * items from whichever instance has some, so small instances share the
+ * device without a launch per step.  Afterwards every context is where
+ * hk_ldlt leaves it, with a bit-identical factor (schoolbook products).
+ * Ordering: the launch runs on the first context's stream after every
+ * context's stream reaches this call; every context's stream then waits
+ * for it.  The contexts must not be used from other threads meanwhile.
+ * idle_limit_s bounds how long the launch waits while no phase of any
+ * instance advances (negative: 2 s); when it runs out the launch returns
+ * and every unfinished instance reports HK_ERR_TIMEOUT at its next
+ * synchronising call (the device stays usable; the context keeps that
+ * error like any other, so a new context repeats the work).
+ * A pivot <= 0 ends that instance only (HK_ERR_NOT_PD as for hk_ldlt). */
+HK_API hk_status hk_ldlt_batch(hk_ctx* const* ctx, int count, double idle_limit_s);
+
+/* a9. Autotuner of hk_ldlt_batch's launch shape.  Times one batch of `count`
+ * instances (beta = 1/m, m = 1, 2, 3, 4 in turn, each of size N, at `bits`)
+ * under each candidate shape (blocks per SM in {2, 3, 4, 6, 8, 12, 16} up to
+ * what fits, items per claim in the largest phases in {1, 4, 8, 16}; the
+ * faster of two runs each) and keeps the fastest for this width and N's
+ * bucket (N <= 128, <= 256, ... doubling), where every later hk_ldlt_batch
+ * whose largest N falls in that bucket uses it (process-wide; untuned
+ * buckets take 8 items and 8, 6 or 4 blocks per SM up to 2048, 6144 and
+ * 8192 bits).  Outputs (host, may be NULL):
+ * the chosen shape and its seconds.  Synchronises the device.  Errors:
+ * HK_ERR_ARG (N outside 1..16384, count outside 1..256, bits not
+ * compiled), HK_ERR_UNSUPPORTED (bits above the batched widths), or the
+ * status of a run that failed (e.g. HK_ERR_NOT_PD when bits is too low for
+ * N); nothing is stored then. */
+HK_API hk_status hk_tune_batch(int device, int bits, int N, int count, int32_t* blocks_per_sm, int32_t* chunk,
+                               double* seconds);
+
 /* Allocation-free LDL^T (no counterpart in the paper: an interface for
  * callers that cannot allow a library to allocate device memory, e.g. a
  * process whose device memory belongs to one allocator or to a fixed budget).
@@ -306,10 +348,9 @@ HK_API hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_
  *          describes it (caller-allocated), written
  *   limit: N * (bits/32 + 2) + bits/32 + 35 <= HK_NOALLOC_SCRATCH_WORDS,
  *          else HK_ERR_ARG (e.g. N <= 1024 at bits <= 24576)
- * The first call on a device looks the array's address up (once per device,
- * with that device current) and keeps it for the life of the library, which
- * therefore must not outlive a cudaDeviceReset of that device; make that
- * first call before any stream capture begins.  Every call shares the array,
+ * Each call looks the array's address up on the current device.  No call
+ * may run on a capturing stream: each one reads the device error word back
+ * and synchronises cuda_stream (below).  Every call shares the array,
  * so calls that overlap on the GPU race: the caller serialises them.  Each
  * call reads the device error word back and synchronises cuda_stream before
  * it returns, and reports device flags with the same status codes as

@@ -28,6 +28,7 @@ STATUS_NAMES = {0: "HK_OK", 1: "HK_ERR_ARG", 2: "HK_ERR_NOMEM", 3: "HK_ERR_CUDA"
 EXPORTS = ["hk_supported_bits", "hk_create", "hk_destroy", "hk_last_error", "hk_moments", "hk_set_moments",
            "hk_ldlt", "hk_plan_block", "hk_inv_block", "hk_lambda1", "hk_lambda1_grad", "hk_export", "hk_fused_batch",
            "hk_div_batch", "hk_set_profiling", "hk_get_profile", "hk_ldlt_noalloc", "hk_batch_run",
+           "hk_ldlt_batch", "hk_tune_batch",
            "hk_set_product_algorithm", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"]
 HK_PRODUCT_AUTO, HK_PRODUCT_SCHOOLBOOK, HK_PRODUCT_NTT, HK_PRODUCT_TENSOR = 0, 1, 2, 3
 HK_NTT_AUTO_MIN_M = 8  # include/hk.h: AUTO uses NTT products from 32 * 8 limbs (8192 bits)
@@ -97,8 +98,10 @@ def load(path=LIB_PATH):
     L.hk_set_product_algorithm.argtypes = [ctypes.c_int]
     L.hk_batch_run.argtypes = [ctypes.c_int, ctypes.POINTER(Instance), ctypes.c_int, ctypes.c_int]
     L.hk_ldlt_noalloc.argtypes = [ctypes.c_int, ctypes.c_int] + [_P] * 6 + [_P]
+    L.hk_ldlt_batch.argtypes = [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_double]
+    L.hk_tune_batch.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I32P, _I32P, _F64P]
     L.hk_get_profile.argtypes = [_P, _F64P, ctypes.c_int]
-    for name in ("hk_set_product_algorithm", "hk_batch_run", "hk_ldlt_noalloc", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
+    for name in ("hk_set_product_algorithm", "hk_batch_run", "hk_ldlt_noalloc", "hk_ldlt_batch", "hk_tune_batch", "hk_set_profiling", "hk_get_profile", "hk_create", "hk_moments", "hk_set_moments", "hk_ldlt", "hk_inv_block", "hk_lambda1",
                  "hk_plan_block", "hk_lambda1_grad", "hk_export", "hk_fused_batch", "hk_div_batch", "hk_moments_gamma", "hk_set_psi_constants", "hk_precision_loss", "hk_alu_peak"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -275,6 +278,26 @@ def hk_ldlt_noalloc(bits, N, mu, factor, stream=None):
     limit and the rule that overlapping calls race."""
     args = [_P(p) for t in (mu, factor) for p in t]
     _check(load().hk_ldlt_noalloc(bits, N, *args, _P(stream or 0)), what="hk_ldlt_noalloc")
+
+
+def hk_ldlt_batch(ctxs, idle_limit_s=-1.0):
+    """Algorithm 1 for several contexts (one device and width, moments set)
+    in one persistent launch; see include/hk.h.  idle_limit_s < 0: 2 s."""
+    arr = (_P * len(ctxs))(*[c.value if isinstance(c, _P) else c for c in ctxs])
+    _check(load().hk_ldlt_batch(arr, len(ctxs), float(idle_limit_s)), ctxs[0] if ctxs else None,
+           what="hk_ldlt_batch")
+
+
+def hk_tune_batch(device, bits, N, count):
+    """Time hk_ldlt_batch's launch shapes on `count` instances of size N at
+    `bits` and keep the fastest for that width and N bucket (include/hk.h).
+    Returns (blocks_per_sm, items_per_claim, seconds)."""
+    b = np.zeros(1, np.int32)
+    g = np.zeros(1, np.int32)
+    t = np.zeros(1, np.float64)
+    _check(load().hk_tune_batch(device, bits, N, count, _ptr(b, ctypes.c_int32), _ptr(g, ctypes.c_int32),
+                                _ptr(t, ctypes.c_double)), what="hk_tune_batch")
+    return int(b[0]), int(g[0]), float(t[0])
 
 
 def hk_batch_run(device, problems, max_concurrent=0):

@@ -121,6 +121,9 @@ struct OpsTable {
   // Algorithm 1 on caller-provided buffers (no allocation): see hk_ldlt_noalloc
   cudaError_t (*ldlt_raw)(MPVec mu, MPVec A, MPVec U, uint32_t* rec, int* rec_meta, int* err, int N,
                           cudaStream_t s, int device);
+  // Algorithm 1 for several contexts of this width in one launch: see hk_ldlt_batch
+  hk_status (*ldlt_batch)(Ctx* const* cs, int count, long long limit_ns, int blocks_per_sm, int chunk);
+  int (*batch_max_blocks)();
 };
 
 const OpsTable* ops_for(int M);

@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <map>
 #include <new>
 #include <thread>
 
@@ -586,6 +588,140 @@ hk_status hk_ldlt(hk_ctx* h) {
   return st;
 }
 
+// Launch shape of the batched factorisation (blocks per SM, items per claim
+// in the largest phases), per width and bucket of the largest N: what
+// hk_tune_batch measured fastest, else a default.
+namespace {
+struct BatchShape {
+  int blocks, chunk;
+};
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, BatchShape> g_tune;
+// untuned: the tuner's picks on one GB300 (8 blocks per SM at 2048 bits, 6
+// at 4096, 4 at 8192; 8 items per claim)
+BatchShape batch_default(int M) { return BatchShape{M <= 2 ? 8 : M <= 6 ? 6 : 4, 8}; }
+int n_bucket(int N) {
+  int b = 0;
+  while (b < 8 && (128 << b) < N) ++b;
+  return b;  // N <= 128, <= 256, ... , > 16384
+}
+BatchShape batch_shape(int M, int max_n) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto it = g_tune.find({M, n_bucket(max_n)});
+  return it == g_tune.end() ? batch_default(M) : it->second;
+}
+}  // namespace
+
+static hk_status ldlt_batch_shaped(hk_ctx* const* hs, int count, double idle_limit_s, const BatchShape* force);
+
+hk_status hk_ldlt_batch(hk_ctx* const* hs, int count, double idle_limit_s) {
+  return ldlt_batch_shaped(hs, count, idle_limit_s, nullptr);
+}
+
+static hk_status ldlt_batch_shaped(hk_ctx* const* hs, int count, double idle_limit_s, const BatchShape* force) {
+  if (!hs || count < 1) return HK_ERR_ARG;
+  std::vector<Ctx*> cs(count);
+  for (int q = 0; q < count; ++q) {
+    hk_status st = enter(hs[q]);
+    if (st != HK_OK) return st;
+    Ctx& c = hs[q]->c;
+    if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_ldlt_batch before the moments");
+    if (q > 0 && (c.device != cs[0]->device || c.M != cs[0]->M))
+      return set_error(c, HK_ERR_ARG, "hk_ldlt_batch: every context must have the first one's device and width");
+    for (int p = 0; p < q; ++p)
+      if (cs[p] == &c) return set_error(c, HK_ERR_ARG, "hk_ldlt_batch: a context appears twice");
+    cs[q] = &c;
+  }
+  if ((cs[0]->M > HK_BATCH_MAX_M))
+    return set_error(*cs[0], HK_ERR_UNSUPPORTED, "hk_ldlt_batch serves widths up to 8192 bits");
+  if (cudaSetDevice(cs[0]->device) != cudaSuccess) return HK_ERR_CUDA;
+  const long long limit_ns =
+      idle_limit_s < 0 ? 2000000000LL : (long long)std::min(idle_limit_s * 1e9, 3.6e12);
+  for (Ctx* c : cs) {
+    c->alg4_k = 0;
+    c->alg4_done = 0;
+  }
+  int max_n = 0;
+  for (Ctx* c : cs) max_n = std::max(max_n, c->N);
+  const BatchShape shape = force ? *force : batch_shape(cs[0]->M, max_n);
+  hk_status st = ops_for(cs[0]->M)->ldlt_batch(cs.data(), count, limit_ns, shape.blocks, shape.chunk);
+  for (Ctx* cp : cs) {
+    Ctx& c = *cp;
+    if (st != HK_OK) break;
+    if ((st = check_cuda(c, cudaMemsetAsync(c.d_err + 1, 0, sizeof(int), c.stream), "clearing")) != HK_OK) break;
+    k_loss_estimate<<<(c.N + 127) / 128, 128, 0, c.stream>>>(c.mu.view(), c.A.view(), c.N, c.n, c.d_err + 1);
+    count_launch(c);
+    if ((st = check_cuda(c, cudaGetLastError(), "k_loss_estimate")) != HK_OK) break;
+    c.stage = ST_LDLT;
+  }
+  return st;
+}
+
+hk_status hk_tune_batch(int device, int bits, int N, int count, int32_t* blocks_per_sm, int32_t* chunk,
+                        double* seconds) {
+  if (!valid_bits(bits) || N < 1 || N > 16384 || count < 1 || count > 256) return HK_ERR_ARG;
+  const int M = bits / 1024;
+  if (M > HK_BATCH_MAX_M) return HK_ERR_UNSUPPORTED;
+  if (cudaSetDevice(device) != cudaSuccess) return HK_ERR_CUDA;
+  const int most = ops_for(M)->batch_max_blocks();
+  if (most < 1) return HK_ERR_CUDA;
+  // the instances: beta = 1/m, m = 1, 2, 3, 4 in turn, all of size N
+  std::vector<hk_ctx*> hs(count, nullptr);
+  std::vector<cudaStream_t> ss(count, nullptr);
+  hk_status st = HK_OK;
+  for (int q = 0; q < count && st == HK_OK; ++q) {
+    if (cudaStreamCreateWithFlags(&ss[q], cudaStreamNonBlocking) != cudaSuccess) {
+      st = HK_ERR_CUDA;
+      break;
+    }
+    st = hk_create(device, ss[q], &hs[q]);
+    if (st == HK_OK) st = hk_moments(hs[q], 1, 1 + q % 4, N, bits);
+  }
+  BatchShape best{0, 0};
+  double best_s = 0;
+  for (int b : {2, 3, 4, 6, 8, 12, 16}) {
+    if (st != HK_OK || b > most) break;
+    for (int g : {1, 4, 8, 16}) {
+      const BatchShape sh{b, g};
+      double t = 0;
+      for (int rep = 0; rep < 2 && st == HK_OK; ++rep) {  // the faster of two runs
+        if (cudaDeviceSynchronize() != cudaSuccess) {
+          st = HK_ERR_CUDA;
+          break;
+        }
+        const auto t0 = std::chrono::steady_clock::now();
+        st = ldlt_batch_shaped(hs.data(), count, -1.0, &sh);
+        if (st == HK_OK && cudaStreamSynchronize(ss[0]) != cudaSuccess) st = HK_ERR_CUDA;
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        t = rep == 0 ? dt : std::min(t, dt);
+      }
+      if (st == HK_OK) {
+        int flags = 0;  // a run that did not finish (timeout, pivot <= 0) does not count
+        for (hk_ctx* h : hs)
+          if (st == HK_OK && (st = read_device_flags(h->c)) != HK_OK) flags = 1;
+        if (flags) break;
+      }
+      if (st == HK_OK && (best.blocks == 0 || t < best_s)) {
+        best = sh;
+        best_s = t;
+      }
+    }
+  }
+  for (int q = 0; q < count; ++q) {
+    if (hs[q]) hk_destroy(hs[q]);
+    if (ss[q]) cudaStreamDestroy(ss[q]);
+  }
+  if (st != HK_OK) return st;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[{M, n_bucket(N)}] = best;
+  }
+  if (blocks_per_sm) *blocks_per_sm = best.blocks;
+  if (chunk) *chunk = best.chunk;
+  if (seconds) *seconds = best_s;
+  return HK_OK;
+}
+
 hk_status hk_alu_peak(int device, int kind, double* per_clk_per_sm) {
   if (kind < 0 || kind > 1 || !per_clk_per_sm) return HK_ERR_ARG;
   if (cudaSetDevice(device) != cudaSuccess) return HK_ERR_CUDA;
@@ -815,38 +951,46 @@ hk_status hk_get_profile(hk_ctx* h, double* out, int cap) {
   return HK_OK;
 }
 
-static void run_instance(int device, hk_instance& in) {
-  const auto t0 = std::chrono::steady_clock::now();
-  hk_status st = HK_OK;
-  cudaStream_t s = nullptr;
+// hk_batch_run in three parts per instance: its stream, context and
+// moments; its factorisation (alone, or in one launch with the instances of
+// its width when that width is a batched one); its block and eigenvalues.
+struct BatchJob {
   hk_ctx* h = nullptr;
-  if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-    in.status = HK_ERR_CUDA;
-    return;
-  }
-  st = hk_create(device, s, &h);
+  cudaStream_t s = nullptr;
+  std::chrono::steady_clock::time_point t0;
+};
+
+static hk_status setup_instance(int device, hk_instance& in, BatchJob& j) {
+  j.t0 = std::chrono::steady_clock::now();
+  if (cudaSetDevice(device) != cudaSuccess || cudaStreamCreateWithFlags(&j.s, cudaStreamNonBlocking) != cudaSuccess)
+    return HK_ERR_CUDA;
+  hk_status st = hk_create(device, j.s, &j.h);
   if (st == HK_OK) {
     if (in.mu_sign && in.mu_exp && in.mu_limbs)
-      st = hk_set_moments(h, in.N, in.bits, in.mu_sign, in.mu_exp, in.mu_limbs, in.beta_num, in.beta_den);
+      st = hk_set_moments(j.h, in.N, in.bits, in.mu_sign, in.mu_exp, in.mu_limbs, in.beta_num, in.beta_den);
     else if (in.gamma_exp && in.gamma_limbs && in.gamma_nc > 0)
-      st = hk_moments_gamma(h, in.beta_num, in.beta_den, in.N, in.bits, in.gamma_nc, in.gamma_exp, in.gamma_limbs);
+      st = hk_moments_gamma(j.h, in.beta_num, in.beta_den, in.N, in.bits, in.gamma_nc, in.gamma_exp, in.gamma_limbs);
     else
-      st = hk_moments(h, in.beta_num, in.beta_den, in.N, in.bits);
+      st = hk_moments(j.h, in.beta_num, in.beta_den, in.N, in.bits);
   }
-  if (st == HK_OK) st = hk_plan_block(h, in.k);
-  if (st == HK_OK) st = hk_ldlt(h);
-  if (st == HK_OK) st = hk_inv_block(h, in.k);
+  if (st == HK_OK) st = hk_plan_block(j.h, in.k);
+  return st;
+}
+
+static void finish_instance(int device, hk_instance& in, BatchJob& j, hk_status st) {
+  cudaSetDevice(device);
+  if (st == HK_OK) st = hk_inv_block(j.h, in.k);
   if (st == HK_OK)
-    st = hk_lambda1(h, in.n_eig, in.lambda_sign, in.lambda_exp, in.lambda_limbs, in.lambda_f64, in.trunc_err_f64);
+    st = hk_lambda1(j.h, in.n_eig, in.lambda_sign, in.lambda_exp, in.lambda_limbs, in.lambda_f64, in.trunc_err_f64);
   in.message[0] = 0;
   if (st != HK_OK) {
-    std::snprintf(in.message, sizeof(in.message), "%s", h ? hk_last_error(h) : "context creation failed");
+    std::snprintf(in.message, sizeof(in.message), "%s", j.h ? hk_last_error(j.h) : "context creation failed");
     if (!in.message[0]) std::snprintf(in.message, sizeof(in.message), "status %d", (int)st);
   }
-  if (h) hk_destroy(h);
-  cudaStreamDestroy(s);
+  if (j.h) hk_destroy(j.h);
+  if (j.s) cudaStreamDestroy(j.s);
   in.status = st;
-  in.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  in.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - j.t0).count();
 }
 
 hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_concurrent) {
@@ -858,13 +1002,54 @@ hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_concurr
     in.status = HK_OK;
   }
   const int workers = (max_concurrent <= 0 || max_concurrent > count) ? count : max_concurrent;
-  std::atomic<int> next(0);
-  std::vector<std::thread> pool;
-  for (int w = 0; w < workers; ++w)
-    pool.emplace_back([&]() {
-      for (int i = next++; i < count; i = next++) run_instance(device, inst[i]);
+  // fn(0 .. items-1) on up to `workers` host threads
+  auto parallel = [&](int items, const std::function<void(int)>& fn) {
+    std::atomic<int> next(0);
+    std::vector<std::thread> pool;
+    for (int w = 0; w < std::min(workers, items); ++w)
+      pool.emplace_back([&]() {
+        for (int q = next++; q < items; q = next++) fn(q);
+      });
+    for (auto& t : pool) t.join();
+  };
+  // waves of at most `workers` instances, so that no more contexts than that
+  // hold device memory at once
+  for (int w0 = 0; w0 < count; w0 += workers) {
+    const int wn = std::min(workers, count - w0);
+    std::vector<BatchJob> jobs(wn);
+    std::vector<hk_status> st(wn, HK_OK);
+    parallel(wn, [&](int q) { st[q] = setup_instance(device, inst[w0 + q], jobs[q]); });
+    // factorisations: the instances of one batched width (two or more) in one
+    // launch; every other instance on its own
+    std::vector<std::vector<int>> tasks;
+    std::map<int, std::vector<int>> by_bits;
+    for (int q = 0; q < wn; ++q) {
+      if (st[q] != HK_OK) continue;
+      if (inst[w0 + q].bits / 1024 <= HK_BATCH_MAX_M)
+        by_bits[inst[w0 + q].bits].push_back(q);
+      else
+        tasks.push_back({q});
+    }
+    for (auto& g : by_bits) {
+      if (g.second.size() >= 2)
+        tasks.push_back(g.second);
+      else
+        tasks.push_back({g.second[0]});
+    }
+    parallel((int)tasks.size(), [&](int t) {
+      const std::vector<int>& v = tasks[t];
+      cudaSetDevice(device);
+      if (v.size() == 1) {
+        st[v[0]] = hk_ldlt(jobs[v[0]].h);
+        return;
+      }
+      std::vector<hk_ctx*> hs;
+      for (int q : v) hs.push_back(jobs[q].h);
+      const hk_status r = hk_ldlt_batch(hs.data(), (int)hs.size(), -1.0);
+      for (int q : v) st[q] = r;
     });
-  for (auto& t : pool) t.join();
+    parallel(wn, [&](int q) { finish_instance(device, inst[w0 + q], jobs[q], st[q]); });
+  }
   for (int i = 0; i < count; ++i)
     if (inst[i].status != HK_OK) return (hk_status)inst[i].status;
   return HK_OK;

@@ -5,6 +5,7 @@
 #include <cstdio>
 
 #include "ctx.h"
+#include "k_batch.cuh"
 #include "k_ldlt.cuh"
 #include "k_tail.cuh"
 #include "tc.cuh"
@@ -528,13 +529,115 @@ struct Ops {
     return cudaGetLastError();
   }
 
+  // Blocks per SM the batched launch can hold (0 above the batched widths).
+  static int batch_max_blocks() {
+    if constexpr (M > HK_BATCH_MAX_M) {
+      return 0;
+    } else {
+      constexpr size_t bsmem = (size_t)HK_BATCH_WARPS * batch_warp_words<M>() * 4;
+      if (allow_smem(k_ldlt_batch<M>, bsmem) != cudaSuccess) return 0;
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ldlt_batch<M>, 32 * HK_BATCH_WARPS, bsmem);
+      return per_sm;
+    }
+  }
+
+  // a9: Algorithm 1 for several contexts of this width in one persistent
+  // launch (k_ldlt_batch).  Each context's moments are ready on its own
+  // stream; the launch runs on the first context's stream after the others'
+  // assemblies, and every context's stream waits for it.  limit_ns bounds
+  // the launch's idle wait (ERR_TIMEOUT in the unfinished instances).
+  static hk_status ldlt_batch(Ctx* const* cs, int count, long long limit_ns, int blocks_per_sm, int chunk) {
+    if (count < 1) return HK_OK;
+    Ctx& c0 = *cs[0];
+    hk_status st;
+    if constexpr (M > HK_BATCH_MAX_M) {
+      return set_error(c0, HK_ERR_UNSUPPORTED, "the batched factorisation serves widths up to 8192 bits");
+    } else {
+      constexpr size_t bsmem = (size_t)HK_BATCH_WARPS * batch_warp_words<M>() * 4;
+      if ((st = check_cuda(c0, allow_smem(k_ldlt_batch<M>, bsmem), "smem attribute")) != HK_OK) return st;
+      std::vector<BatchInst> hb(count);
+      size_t state_words = 0;
+      for (int q = 0; q < count; ++q) state_words += 4 * (size_t)cs[q]->N;
+      // device block: instances | control | per-instance phase, tickets, done counts
+      const size_t inst_bytes = ((size_t)count * sizeof(BatchInst) + 15) / 16 * 16;
+      const size_t bytes = inst_bytes + sizeof(BatchCtl) + state_words * 4;
+      char* blk = nullptr;
+      if ((st = check_cuda(c0, cudaMallocAsync((void**)&blk, bytes, c0.stream), "allocating the batch state")) != HK_OK)
+        return st;
+      int* state = reinterpret_cast<int*>(blk + inst_bytes + sizeof(BatchCtl));
+      size_t off = 0;
+      std::vector<cudaEvent_t> evs;
+      auto event = [&](cudaStream_t on) -> cudaError_t {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r == cudaSuccess) r = cudaEventRecord(e, on);
+        if (r == cudaSuccess) evs.push_back(e);
+        return r;
+      };
+      for (int q = 0; q < count && st == HK_OK; ++q) {
+        Ctx& c = *cs[q];
+        c.cols_marked = false;
+        const int N = c.N;
+        const int64_t tri = (int64_t)N * (N + 1) / 2;
+        if (c.A.count != tri || c.A.n != n) {
+          dev_free(c.A);
+          if ((st = check_cuda(c, dev_alloc(c.A, tri, n), "allocating the factor")) != HK_OK) break;
+        }
+        if (c.U.count != N || c.U.n != n) {
+          dev_free(c.U);
+          if ((st = check_cuda(c, dev_alloc(c.U, N, n), "allocating the pivot column")) != HK_OK) break;
+        }
+        if (!c.rec) {
+          if ((st = check_cuda(c, cudaMalloc(&c.rec, (size_t)n * 4 + 64), "allocating the reciprocal")) != HK_OK) break;
+          c.rec_meta = reinterpret_cast<int*>(c.rec + n);
+        }
+        const int64_t work = tri * (n / 4);
+        const int grid = (int)std::min<int64_t>((work + 255) / 256, 8 * sm_count(c.device) * 8);
+        k_assemble<M><<<grid, 256, 0, c.stream>>>(c.mu.view(), c.A.view(), N);
+        count_launch(c);
+        if (q > 0) {
+          if ((st = check_cuda(c, event(c.stream), "event")) != HK_OK) break;
+          cudaStreamWaitEvent(c0.stream, evs.back(), 0);
+        }
+        hb[q] = BatchInst{c.A.view(), c.U.view(), c.rec, c.rec_meta, c.d_err, state + off, N};
+        off += 4 * (size_t)N;
+      }
+      cudaStream_t s = c0.stream;
+      if (st == HK_OK) {
+        // pageable source: the copy has read it when the call returns
+        st = check_cuda(c0, cudaMemcpyAsync(blk, hb.data(), (size_t)count * sizeof(BatchInst), cudaMemcpyHostToDevice, s),
+                        "copying the batch");
+      }
+      if (st == HK_OK)
+        st = check_cuda(c0, cudaMemsetAsync(blk + inst_bytes, 0, sizeof(BatchCtl) + state_words * 4, s), "clearing");
+      if (st == HK_OK) {
+        // blocks_per_sm blocks on every SM (at most what fits)
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ldlt_batch<M>, 32 * HK_BATCH_WARPS, bsmem);
+        const int grid = std::max(1, std::min(per_sm, blocks_per_sm)) * sm_count(c0.device);
+        k_ldlt_batch<M><<<grid, 32 * HK_BATCH_WARPS, bsmem, s>>>(reinterpret_cast<const BatchInst*>(blk), count,
+                                                                 reinterpret_cast<BatchCtl*>(blk + inst_bytes), limit_ns,
+                                                                 std::max(1, chunk));
+        count_launch(c0);
+        st = check_cuda(c0, cudaGetLastError(), "k_ldlt_batch");
+      }
+      if (st == HK_OK && (st = check_cuda(c0, event(s), "event")) == HK_OK)
+        for (int q = 1; q < count; ++q) cudaStreamWaitEvent(cs[q]->stream, evs.back(), 0);
+      cudaFreeAsync(blk, s);
+      for (cudaEvent_t e : evs) cudaEventDestroy(e);  // released once their work is done
+      return st;
+    }
+  }
+
   static hk_status inv_block(Ctx& c);
   static hk_status lambda(Ctx& c, int n_eig);
   static hk_status grad(Ctx& c, int32_t* sgn, int32_t* exp, uint32_t* mant, double* f64);
 
   static OpsTable table() {
     return OpsTable{M,           &Ops::ldlt,        &Ops::inv_block, &Ops::lambda, &Ops::grad,
-                    &Ops::fused_batch, &Ops::div_batch, &Ops::ldlt_raw};
+                    &Ops::fused_batch, &Ops::div_batch, &Ops::ldlt_raw, &Ops::ldlt_batch,
+                    &Ops::batch_max_blocks};
   }
 };
 

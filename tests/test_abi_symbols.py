@@ -74,3 +74,29 @@ def test_plan_block_needs_a_context():
     L = hk.load()
     assert L.hk_plan_block(None, 32) == hk.HK_ERR_ARG
     assert L.hk_plan_block(None, 0) == hk.HK_ERR_ARG
+
+
+def test_batch_launch_rejects_empty_and_null_contexts():
+    """hk_ldlt_batch answers HK_ERR_ARG for no contexts, a null array or a
+    null context in the array, before it touches a device."""
+    import ctypes
+
+    import paper_1810_01478_gb300 as hk
+    L = hk.load()
+    assert L.hk_ldlt_batch(None, 0, -1.0) == hk.HK_ERR_ARG
+    assert L.hk_ldlt_batch(None, 2, -1.0) == hk.HK_ERR_ARG
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.hk_ldlt_batch(arr, 2, -1.0) == hk.HK_ERR_ARG
+    assert L.hk_ldlt_batch(arr, 0, -1.0) == hk.HK_ERR_ARG
+
+
+def test_batch_tuner_rejects_bad_arguments():
+    """hk_tune_batch answers HK_ERR_ARG / HK_ERR_UNSUPPORTED for sizes and
+    widths it does not serve before it touches a device."""
+    import paper_1810_01478_gb300 as hk
+    L = hk.load()
+    assert L.hk_tune_batch(0, 4096, 0, 4, None, None, None) == hk.HK_ERR_ARG
+    assert L.hk_tune_batch(0, 4096, 64, 0, None, None, None) == hk.HK_ERR_ARG
+    assert L.hk_tune_batch(0, 4096, 64, 257, None, None, None) == hk.HK_ERR_ARG
+    assert L.hk_tune_batch(0, 1000, 64, 4, None, None, None) == hk.HK_ERR_ARG
+    assert L.hk_tune_batch(0, 12288, 64, 4, None, None, None) == hk.HK_ERR_UNSUPPORTED
