@@ -141,8 +141,9 @@ HK_API hk_status hk_ldlt(hk_ctx* ctx);
  * column i of L that the trailing update already holds.  hk_inv_block with the
  * same k then runs only the remaining steps.  Every update is the same
  * truncated operation, in the same order for each entry, so X and S are bit
- * for bit those of the unplanned call.  0 <= k <= 64; a k above N is
- * HK_ERR_ARG at hk_ldlt.  Enqueues nothing. */
+ * for bit those of the unplanned call.  hk_ldlt_batch runs every step of
+ * Algorithm 4 for a planned context inside its launch.  0 <= k <= 64; a k
+ * above N is HK_ERR_ARG at hk_ldlt or hk_ldlt_batch.  Enqueues nothing. */
 HK_API hk_status hk_plan_block(hk_ctx* ctx, int k);
 
 /* a5-a6. X = first k columns of L^{-1} by Algorithm 4 (Sec. 4.4; row
@@ -306,8 +307,12 @@ HK_API hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_
  * factorisation is a chain of phases (the pivot's reciprocal, the column
  * scale, the trailing update of each step); the launch's warps take work
  * items from whichever instance has some, so small instances share the
- * device without a launch per step.  Afterwards every context is where
- * hk_ldlt leaves it, with a bit-identical factor (schoolbook products).
+ * device without a launch per step.  A context planned with a block size
+ * k (hk_plan_block) also gets Algorithm 4's X = L^-1[:, :k] inside the
+ * launch (step i's updates share step i's trailing phase), so its
+ * hk_inv_block(k) goes straight to the block.  Afterwards every context is
+ * where hk_ldlt leaves it, with a bit-identical factor and X (schoolbook
+ * products).
  * Ordering: the launch runs on the first context's stream after every
  * context's stream reaches this call; every context's stream then waits
  * for it.  The contexts must not be used from other threads meanwhile.

@@ -626,6 +626,7 @@ static hk_status ldlt_batch_shaped(hk_ctx* const* hs, int count, double idle_lim
     if (st != HK_OK) return st;
     Ctx& c = hs[q]->c;
     if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_ldlt_batch before the moments");
+    if (c.plan_k > c.N) return set_error(c, HK_ERR_ARG, "the planned k exceeds N");
     if (q > 0 && (c.device != cs[0]->device || c.M != cs[0]->M))
       return set_error(c, HK_ERR_ARG, "hk_ldlt_batch: every context must have the first one's device and width");
     for (int p = 0; p < q; ++p)
@@ -653,6 +654,12 @@ static hk_status ldlt_batch_shaped(hk_ctx* const* hs, int count, double idle_lim
     count_launch(c);
     if ((st = check_cuda(c, cudaGetLastError(), "k_loss_estimate")) != HK_OK) break;
     c.stage = ST_LDLT;
+    // Algorithm 4 ran inside the launch for the planned k: hk_inv_block(k)
+    // goes straight to the block
+    if (c.plan_k > 0 && c.N > 1) {
+      c.alg4_k = c.plan_k;
+      c.alg4_done = c.N - 1;
+    }
   }
   return st;
 }

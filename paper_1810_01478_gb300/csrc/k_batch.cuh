@@ -8,7 +8,11 @@
 //   phase 2 + 2i     trailing update of step i                   (m(m+1)/2 items)
 //                    item 0 is the entry (i+1, i+1) = d_{i+1}; the warp that
 //                    forms it goes on to the reciprocal of d_{i+1} (the
-//                    look-ahead of Alg. 2 inside the update)
+//                    look-ahead of Alg. 2 inside the update); then, for an
+//                    instance planned with a block size k, step i of
+//                    Algorithm 4 (Sec. 4.4) on X = L^-1[:, :k]: it needs
+//                    only column i of L (final after the scale) and row i
+//                    of X (final after step i - 1), so it shares the phase
 //   phase 2N - 1     finished
 // Every item of a phase depends only on phases before it, so any warp may
 // take any item of an instance's current phase.  Warps claim items with an
@@ -38,7 +42,10 @@ struct BatchInst {
   int* rec_meta;     // [0]: its shift
   int* err;          // the instance's error word (ErrBits)
   int* state;        // [0] phase, [1 .. 2N-1] tickets, [2N .. 4N-2] done counts
+  MPVec X;           // N x k, row major: Algorithm 4's X, first k columns of
+                     // the identity on entry (k = 0: no Algorithm 4)
   int N;
+  int k;
 };
 
 // Launch-wide control words.
@@ -110,10 +117,15 @@ __device__ __forceinline__ void stage_l2(uint32_t* dst, const uint32_t* src) {
   for (int k = 0; k < M; ++k) dst[lane_id() * M + k] = v[k];
 }
 
-__device__ __forceinline__ int64_t batch_items(int N, int ph) {
+// Algorithm 4's updates in step i: per row j > i, the columns c < min(k, i)
+// and, while i < k, the new entry X[j][i] = -L[j][i]
+__device__ __forceinline__ int batch_alg4_per_row(int k, int i) { return k <= 0 ? 0 : (i < k ? i + 1 : k); }
+
+__device__ __forceinline__ int64_t batch_items(const BatchInst& b, int ph) {
   if (ph == 0) return 1;
-  const int64_t m = N - 1 - ((ph - 1) >> 1);
-  return (ph & 1) ? m : m * (m + 1) / 2;
+  const int i = (ph - 1) >> 1;
+  const int64_t m = b.N - 1 - i;
+  return (ph & 1) ? m : m * (m + 1) / 2 + m * batch_alg4_per_row(b.k, i);
 }
 
 // Reciprocal of a pivot held in registers (dc, sign sgn): R and its shift
@@ -172,6 +184,40 @@ __device__ void batch_scale(const BatchInst& b, int i, int64_t r, uint32_t* w) {
 // Trailing update of step i, entry t of the packed trailing triangle:
 // A[r][c] = trunc(A[r][c] - U[c] B_i[r]); entry 0 (= d_{i+1}) also takes the
 // reciprocal of the next pivot.
+// Algorithm 4, step i, update u of the step (row j = i + 1 + u / per_row,
+// column c = u % per_row):  X[j][i] = -L[j][i] when c = i < k, else
+// X[j][c] = trunc(X[j][c] - L[j][i] X[i][c]).
+template <int M>
+__device__ void batch_alg4(const BatchInst& b, int i, int64_t u, uint32_t* w) {
+  constexpr int n = 32 * M;
+  const int N = b.N, k = b.k;
+  const int per_row = batch_alg4_per_row(k, i);
+  const int cols = i < k ? i : k;
+  const int64_t j = i + 1 + u / per_row;
+  const int c = (int)(u % per_row);
+  const int64_t fpos = tri_pos(N, j, i);
+  if (c == cols) {
+    uint32_t v[M];
+    load_chunk_l2<M>(b.A.mant + fpos * n, v);
+    const bool zero = __shfl_sync(FULL, v[M - 1], 31) == 0u;
+    const Result r{zero ? 0 : (__ldcg(b.A.sgn + fpos) ^ 1), __ldcg(b.A.exp + fpos), zero};
+    store_result<M>(b.X, j * k + i, r, v);
+    return;
+  }
+  const int64_t apos = j * k + c, ypos = (int64_t)i * k + c;
+  WarpSmem<M> sm(w);
+  stage_l2<M>(sm.ys, b.X.mant + ypos * n);
+  stage_l2<M>(sm.sa, b.X.mant + apos * n);
+  uint32_t xc[M], o[M];
+  load_chunk_l2<M>(b.A.mant + fpos * n, xc);
+  const int sl = __ldcg(b.A.sgn + fpos), el = __ldcg(b.A.exp + fpos);
+  const int sy = __ldcg(b.X.sgn + ypos), ey = __ldcg(b.X.exp + ypos);
+  const int sa = __ldcg(b.X.sgn + apos), ea = __ldcg(b.X.exp + apos);
+  __syncwarp();
+  const Result r = fused_staged<M>(sm, xc, sl, el, sy, ey, sa, ea, o);
+  store_result<M>(b.X, apos, r, o);
+}
+
 template <int M>
 __device__ void batch_trailing(const BatchInst& b, int i, int64_t t, uint32_t* w) {
   constexpr int n = 32 * M;
@@ -223,7 +269,7 @@ __device__ __forceinline__ bool batch_claim(const BatchInst& b, int chunk, bool 
                                             int64_t& last) {
   const int q = ld_acquire_gpu(b.state);
   if (q >= 2 * b.N - 1) return false;
-  const int64_t cnt = batch_items(b.N, q);
+  const int64_t cnt = batch_items(b, q);
   const int64_t chunks = batch_chunks(cnt, chunk);
   int* tick = b.state + 1 + q;
   if (precheck && ld_relaxed_gpu(tick) >= chunks) return false;  // all claimed: take no ticket
@@ -315,14 +361,19 @@ __global__ void __launch_bounds__(32 * HK_BATCH_WARPS)
         const int i = (ph - 1) >> 1;
         batch_scale<M>(b, i, i + 1 + item, w);
       } else {
-        batch_trailing<M>(b, (ph - 2) >> 1, item, w);
+        const int i = (ph - 2) >> 1;
+        const int64_t m = b.N - 1 - i, T = m * (m + 1) / 2;
+        if (item < T)
+          batch_trailing<M>(b, i, item, w);
+        else
+          batch_alg4<M>(b, i, item - T, w);
       }
       __syncwarp();
     }
     // release: the warp's writes (ordered before lane 0's by the warp
     // barrier), then one count for the chunk
     if (lane == 0) {
-      const int64_t cnt = batch_items(b.N, ph);
+      const int64_t cnt = batch_items(b, ph);
       int* done = b.state + 2 * b.N + ph;
       const int k = (int)(last - first);
       if (atom_add_acq_rel_gpu(done, k) + k == cnt) {

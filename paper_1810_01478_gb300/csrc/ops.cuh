@@ -596,11 +596,24 @@ struct Ops {
         const int grid = (int)std::min<int64_t>((work + 255) / 256, 8 * sm_count(c.device) * 8);
         k_assemble<M><<<grid, 256, 0, c.stream>>>(c.mu.view(), c.A.view(), N);
         count_launch(c);
+        // a planned block size (hk_plan_block): Algorithm 4 runs inside the
+        // launch, X starts as the first k columns of the identity
+        const int pk = c.plan_k;
+        if (pk > 0) {
+          if (c.X.count != (int64_t)N * pk || c.X.n != n) {
+            dev_free(c.X);
+            if ((st = check_cuda(c, dev_alloc(c.X, (int64_t)N * pk, n), "allocating X")) != HK_OK) break;
+          }
+          const int64_t xw = (int64_t)N * pk * n;
+          k_x_init<M><<<(int)std::min<int64_t>((xw + 255) / 256, 4096), 256, 0, c.stream>>>(c.X.view(), N, pk);
+          count_launch(c);
+        }
         if (q > 0) {
           if ((st = check_cuda(c, event(c.stream), "event")) != HK_OK) break;
           cudaStreamWaitEvent(c0.stream, evs.back(), 0);
         }
-        hb[q] = BatchInst{c.A.view(), c.U.view(), c.rec, c.rec_meta, c.d_err, state + off, N};
+        hb[q] = BatchInst{c.A.view(), c.U.view(), c.rec, c.rec_meta, c.d_err, state + off,
+                          pk > 0 ? c.X.view() : MPVec{}, N, pk};
         off += 4 * (size_t)N;
       }
       cudaStream_t s = c0.stream;

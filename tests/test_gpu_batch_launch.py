@@ -5,6 +5,10 @@ in one persistent launch.
   at N = 512 and 768, 4096 bits, and N = 256, 8192 bits) or, for instances
   without a stored digest, to hk_ldlt's on the same moments, across uneven
   N (1, 2, 33, 130 ...) and several beta.
+* Instances planned with a block size k (hk_plan_block) also run Algorithm 4
+  inside the launch: X = L^-1[:, :k] is bit-identical to the oracle's
+  (stored X digests, k = 32 at N = 512 and k = 16 at N = 256, 8192 bits) or
+  to the single path's (hk_ldlt, then hk_inv_block(k)).
 * A non-positive pivot (moments all 1: H is the rank-one all-ones matrix,
   so d_1 = 0) ends that instance only, with HK_ERR_NOT_PD; the others in the
   same launch are unaffected.
@@ -17,7 +21,7 @@ import os
 
 import pytest
 
-from tests.digest import factor_digest
+from tests.digest import factor_digest, x_digest
 
 pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -37,11 +41,23 @@ def single_digest(hk, beta, N, bits):
         return factor_digest(r, hk, N)
 
 
+def single_x_digest(hk, beta, N, bits, k):
+    with hk.Hankel(0) as r:
+        r.moments(beta[0], beta[1], N, bits)
+        r.ldlt()
+        r.inv_block(k)
+        return x_digest(r, hk, N, k)
+
+
 def run_batch(hk, specs, limit=-1.0):
+    """specs: (beta, N, bits, golden name or None[, planned k])"""
     hs = []
-    for beta, N, bits, _ in specs:
+    for spec in specs:
+        beta, N, bits = spec[:3]
         h = hk.Hankel(0)
         h.moments(beta[0], beta[1], N, bits)
+        if len(spec) > 4 and spec[4]:
+            hk.hk_plan_block(h.ctx, spec[4])
         hs.append(h)
     hk.hk_ldlt_batch([h.ctx for h in hs], limit)
     return hs
@@ -52,17 +68,22 @@ def test_batch_launch_factors_are_bit_exact(width):
     import paper_1810_01478_gb300 as hk
     hk.load()
     if width == 4096:
-        specs = [((1, 2), 512, 4096, "c5_512_4096"), ((1, 3), 64, 4096, None), ((1, 1), 1, 4096, None),
-                 ((1, 2), 768, 4096, "c5_768_4096"), ((1, 2), 33, 4096, None), ((1, 4), 130, 4096, None),
-                 ((1, 2), 2, 4096, None)]
+        specs = [((1, 2), 512, 4096, "c5_512_4096", 32), ((1, 3), 64, 4096, None, 8), ((1, 1), 1, 4096, None, 1),
+                 ((1, 2), 768, 4096, "c5_768_4096", 0), ((1, 2), 33, 4096, None, 33), ((1, 4), 130, 4096, None, 0),
+                 ((1, 2), 2, 4096, None, 2)]
     else:
-        specs = [((1, 2), 256, 8192, "c2"), ((1, 1), 100, 8192, None), ((1, 3), 31, 8192, None)]
+        specs = [((1, 2), 256, 8192, "c2", 16), ((1, 1), 100, 8192, None, 5), ((1, 3), 31, 8192, None, 0)]
     hs = run_batch(hk, specs)
     try:
-        for (beta, N, bits, g), h in zip(specs, hs):
+        for (beta, N, bits, g, k), h in zip(specs, hs):
             got = factor_digest(h, hk, N)
             want = golden(g)["factor_sha256"] if g else single_digest(hk, beta, N, bits)
             assert got == want, (beta, N, bits)
+            if k:
+                h.inv_block(k)
+                gx = golden(g) if g else None
+                want_x = gx["x_sha256"] if gx and gx["k"] == k else single_x_digest(hk, beta, N, bits, k)
+                assert x_digest(h, hk, N, k) == want_x, (beta, N, bits, k)
     finally:
         for h in hs:
             h.close()
@@ -99,10 +120,10 @@ def test_batch_launch_non_pd_instance_ends_alone():
 def test_batch_launch_wait_limit_reports_timeout_and_device_recovers():
     import paper_1810_01478_gb300 as hk
     hk.load()
-    specs = [((1, 2), 64, 4096, None), ((1, 3), 80, 4096, None), ((1, 1), 72, 4096, None)]
+    specs = [((1, 2), 64, 4096, None), ((1, 3), 80, 4096, None, 16), ((1, 1), 72, 4096, None)]
     hs = run_batch(hk, specs, limit=0.0)
     try:
-        for (beta, N, bits, _), h in zip(specs, hs):
+        for (beta, N, bits, *_), h in zip(specs, hs):
             with pytest.raises(hk.HKError) as ei:
                 h.export(hk.HK_D, 0, N)
             assert ei.value.status == hk.HK_ERR_TIMEOUT
@@ -111,7 +132,7 @@ def test_batch_launch_wait_limit_reports_timeout_and_device_recovers():
             h.close()
     hs = run_batch(hk, specs)
     try:
-        for (beta, N, bits, _), h in zip(specs, hs):
+        for (beta, N, bits, *_), h in zip(specs, hs):
             assert factor_digest(h, hk, N) == single_digest(hk, beta, N, bits)
     finally:
         for h in hs:
