@@ -26,9 +26,10 @@
 //
 // Data written during the launch (the factor, U, the reciprocal) is read
 // with L2-only loads (ld.global.cg), after an acquire load of the phase.
-// Products are schoolbook (the widths this form serves are below the NTT
-// widths), and every entry goes through the same exact operations in the
-// same step order as the step-by-step launches, so the factor is bit-identical.
+// Products are schoolbook at every width this form serves (up to 8192
+// bits, where the step-by-step launches take NTT products instead); every
+// product is exact and every entry goes through the same truncated
+// operations in the same step order, so the factor is bit-identical.
 #pragma once
 #include "k_ldlt.cuh"
 
