@@ -326,7 +326,7 @@ HK_API hk_status hk_ldlt_batch(hk_ctx* const* ctx, int count, double idle_limit_
 
 /* a9. Autotuner of hk_ldlt_batch's launch shape.  Times one batch of `count`
  * instances (beta = 1/m, m = 1, 2, 3, 4 in turn, each of size N, at `bits`)
- * under each candidate shape (blocks per SM in {2, 3, 4, 6, 8, 12, 16} up to
+ * under each candidate shape (blocks per SM in {1, 2, 3, 4, 6, 8, 12, 16} up to
  * what fits, items per claim in the largest phases in {1, 4, 8, 16}; the
  * faster of two runs each) and keeps the fastest for this width and N's
  * bucket (N <= 128, <= 256, ... doubling), where every later hk_ldlt_batch

@@ -686,7 +686,7 @@ hk_status hk_tune_batch(int device, int bits, int N, int count, int32_t* blocks_
   }
   BatchShape best{0, 0};
   double best_s = 0;
-  for (int b : {2, 3, 4, 6, 8, 12, 16}) {
+  for (int b : {1, 2, 3, 4, 6, 8, 12, 16}) {
     if (st != HK_OK || b > most) break;
     for (int g : {1, 4, 8, 16}) {
       const BatchShape sh{b, g};
@@ -719,6 +719,7 @@ hk_status hk_tune_batch(int device, int bits, int N, int count, int32_t* blocks_
     if (ss[q]) cudaStreamDestroy(ss[q]);
   }
   if (st != HK_OK) return st;
+  if (best.blocks < 1) return HK_ERR_CUDA;  // no shape could be timed
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[{M, n_bucket(N)}] = best;

@@ -165,7 +165,7 @@ def test_tuner_picks_a_shape_and_batches_stay_exact():
     import paper_1810_01478_gb300 as hk
     hk.load()
     b, g, t = hk.hk_tune_batch(0, 2048, 48, 6)
-    assert b in (2, 3, 4, 6, 8, 12, 16) and g in (1, 4, 8, 16) and t > 0
+    assert b in (1, 2, 3, 4, 6, 8, 12, 16) and g in (1, 4, 8, 16) and t > 0
     # a later batch whose largest N is in the same bucket takes the tuned shape
     specs = [((1, 2), 40, 2048, None), ((1, 3), 48, 2048, None), ((1, 1), 7, 2048, None)]
     hs = run_batch(hk, specs)
