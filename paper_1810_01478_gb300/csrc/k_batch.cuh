@@ -31,6 +31,7 @@
 // product is exact and every entry goes through the same truncated
 // operations in the same step order, so the factor is bit-identical.
 #pragma once
+#include "batch_sched.h"
 #include "k_ldlt.cuh"
 
 namespace hk {
@@ -118,16 +119,7 @@ __device__ __forceinline__ void stage_l2(uint32_t* dst, const uint32_t* src) {
   for (int k = 0; k < M; ++k) dst[lane_id() * M + k] = v[k];
 }
 
-// Algorithm 4's updates in step i: per row j > i, the columns c < min(k, i)
-// and, while i < k, the new entry X[j][i] = -L[j][i]
-__device__ __forceinline__ int batch_alg4_per_row(int k, int i) { return k <= 0 ? 0 : (i < k ? i + 1 : k); }
-
-__device__ __forceinline__ int64_t batch_items(const BatchInst& b, int ph) {
-  if (ph == 0) return 1;
-  const int i = (ph - 1) >> 1;
-  const int64_t m = b.N - 1 - i;
-  return (ph & 1) ? m : m * (m + 1) / 2 + m * batch_alg4_per_row(b.k, i);
-}
+__device__ __forceinline__ int64_t batch_items(const BatchInst& b, int ph) { return batch_phase_items(b.N, b.k, ph); }
 
 // Reciprocal of a pivot held in registers (dc, sign sgn): R and its shift
 // into the instance's buffers; a pivot <= 0 sets ERR_NOT_PD instead.
@@ -192,10 +184,10 @@ template <int M>
 __device__ void batch_alg4(const BatchInst& b, int i, int64_t u, uint32_t* w) {
   constexpr int n = 32 * M;
   const int N = b.N, k = b.k;
-  const int per_row = batch_alg4_per_row(k, i);
   const int cols = i < k ? i : k;
-  const int64_t j = i + 1 + u / per_row;
-  const int c = (int)(u % per_row);
+  int64_t j;
+  int c;
+  batch_alg4_item(k, i, u, j, c);
   const int64_t fpos = tri_pos(N, j, i);
   if (c == cols) {
     uint32_t v[M];
@@ -245,20 +237,6 @@ __device__ void batch_trailing(const BatchInst& b, int i, int64_t t, uint32_t* w
   if (t == 0) batch_recip<M>(b, o, res.sgn, w);
 }
 
-// Items of a phase are claimed in chunks: chunk 0 is item 0 alone (in a
-// trailing phase it carries the next pivot's reciprocal, the step's
-// critical path), chunk k >= 1 holds items 1 + (k-1) G .. k G, with G
-// growing with the phase up to `chunk` so that large phases pay one claim
-// per G updates while small ones keep every warp busy.
-__device__ __forceinline__ int64_t batch_group(int64_t cnt, int chunk) {
-  const int64_t g = cnt >= 4096 ? chunk : cnt >= 1024 ? (chunk + 1) / 2 : cnt >= 256 ? (chunk + 3) / 4 : 1;
-  return g < 1 ? 1 : g;
-}
-__device__ __forceinline__ int64_t batch_chunks(int64_t cnt, int chunk) {
-  const int64_t g = batch_group(cnt, chunk);
-  return cnt <= 1 ? cnt : 1 + (cnt - 1 + g - 1) / g;
-}
-
 __device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v) {
   int old;
   asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
@@ -276,10 +254,8 @@ __device__ __forceinline__ bool batch_claim(const BatchInst& b, int chunk, bool 
   if (precheck && ld_relaxed_gpu(tick) >= chunks) return false;  // all claimed: take no ticket
   const int64_t t = atomicAdd(tick, 1);
   if (t >= chunks) return false;
-  const int64_t g = batch_group(cnt, chunk);
   ph = q;
-  first = t == 0 ? 0 : 1 + (t - 1) * g;
-  last = t == 0 ? 1 : (first + g < cnt ? first + g : cnt);
+  batch_chunk_range(cnt, chunk, t, first, last);
   return true;
 }
 
