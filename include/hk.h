@@ -242,8 +242,9 @@ HK_API hk_status hk_get_profile(hk_ctx* ctx, double* out, int cap);
 #define HK_PRODUCT_TENSOR 3
 #define HK_NTT_AUTO_MIN_M 8
 #define HK_TC_MIN_M 8
-/* widest width of hk_ldlt_batch: 1024 * HK_BATCH_MAX_M bits */
+/* widest width of hk_ldlt_batch: 1024 * HK_BATCH_MAX_M bits; largest N */
 #define HK_BATCH_MAX_M 8
+#define HK_BATCH_MAX_N 32768
 #define HK_TC_AUTO_MIN_M 12
 /* With tensor-core products, steps of Algorithm 1 whose trailing triangle has
  * fewer rows than this keep NTT products (too few 128-row work items to fill
@@ -303,7 +304,8 @@ HK_API hk_status hk_batch_run(int device, hk_instance* inst, int count, int max_
 /* a9. Algorithm 1 (Sec. 4.3) for `count` contexts in ONE persistent launch.
  * Every context must be on one device, at one width of at most
  * HK_BATCH_MAX_M * 1024 bits (else HK_ERR_ARG / HK_ERR_UNSUPPORTED), with
- * its moments set (else HK_ERR_ORDER), and appear once.  Each instance's
+ * its moments set (else HK_ERR_ORDER), N <= HK_BATCH_MAX_N and a planned k
+ * <= N (else HK_ERR_ARG), and appear once.  Each instance's
  * factorisation is a chain of phases (the pivot's reciprocal, the column
  * scale, the trailing update of each step); the launch's warps take work
  * items from whichever instance has some, so small instances share the

@@ -627,6 +627,8 @@ static hk_status ldlt_batch_shaped(hk_ctx* const* hs, int count, double idle_lim
     Ctx& c = hs[q]->c;
     if (c.stage < ST_MOMENTS) return set_error(c, HK_ERR_ORDER, "hk_ldlt_batch before the moments");
     if (c.plan_k > c.N) return set_error(c, HK_ERR_ARG, "the planned k exceeds N");
+    // the launch's per-phase claim and done counters are 32-bit
+    if (c.N > HK_BATCH_MAX_N) return set_error(c, HK_ERR_ARG, "hk_ldlt_batch serves N up to HK_BATCH_MAX_N");
     if (q > 0 && (c.device != cs[0]->device || c.M != cs[0]->M))
       return set_error(c, HK_ERR_ARG, "hk_ldlt_batch: every context must have the first one's device and width");
     for (int p = 0; p < q; ++p)
