@@ -63,11 +63,14 @@ def run_batch(hk, specs, limit=-1.0):
     return hs
 
 
-@pytest.mark.parametrize("width", [4096, 8192])
+@pytest.mark.parametrize("width", [1024, 3072, 4096, 8192])
 def test_batch_launch_factors_are_bit_exact(width):
     import paper_1810_01478_gb300 as hk
     hk.load()
-    if width == 4096:
+    if width in (1024, 3072):  # odd limbs per lane: scalar loads
+        specs = [((1, 2), 48, width, None, 8), ((1, 3), 17, width, None, 0), ((1, 1), 1, width, None, 0),
+                 ((1, 4), 40, width, None, 40)]
+    elif width == 4096:
         specs = [((1, 2), 512, 4096, "c5_512_4096", 32), ((1, 3), 64, 4096, None, 8), ((1, 1), 1, 4096, None, 1),
                  ((1, 2), 768, 4096, "c5_768_4096", 0), ((1, 2), 33, 4096, None, 33), ((1, 4), 130, 4096, None, 0),
                  ((1, 2), 2, 4096, None, 2)]
